@@ -1,0 +1,887 @@
+// hd_api.cu -- host side of the C ABI declared in include/hd.h.
+//
+// Plans the workspace layout, uploads the replicas, and drives the per-phase
+// kernels (captured in CUDA graphs) or the persistent kernel.  Every call
+// returns an hd_status; the first error is kept on the context.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hd_internal.cuh"
+#include "hd_launch.h"
+
+using namespace hd;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct Plan {
+    int nrep = 0, natom = 0, ntile = 0, maxnb = 0, cell_cap = 0, ncell = 0, block = 128, prec = 0;
+    std::vector<RepDev> rep;
+    std::vector<int> tile_rep, tile_start, tile_n;
+    size_t bytes = 0;
+    // offsets
+    size_t o_rep, o_st, o_sc, o_trep, o_tstart, o_tn, o_part, o_qpart, o_kpart;
+    size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
+    size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
+    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt;
+};
+
+size_t take(size_t &cur, size_t bytes) {
+    size_t o = (cur + ALIGN - 1) / ALIGN * ALIGN;
+    cur = o + bytes;
+    return o;
+}
+
+bool valid_desc(const hd_replica_desc &d, std::string &why) {
+    char b[160];
+    if (d.dim != 2 && d.dim != 3) { why = "dim must be 2 or 3"; return false; }
+    if (d.n_atoms <= 0 || !d.pos || !d.role || !d.type) { why = "empty replica or NULL arrays"; return false; }
+    if (d.kT <= 0.0 || d.gamma < 0.0) { why = "kT must be > 0 and gamma >= 0"; return false; }
+    if (d.m_exp < 1) { why = "m_exp must be >= 1"; return false; }
+    for (int a = 0; a < d.dim - 1; ++a)
+        if (!d.periodic[a] || !(d.box[a] > 0.0)) {
+            snprintf(b, sizeof b, "in-plane axis %d must be periodic with a positive length", a);
+            why = b;
+            return false;
+        }
+    if (d.periodic[d.dim - 1] || (d.dim == 2 && d.periodic[2])) { why = "the vertical axis must be open"; return false; }
+    for (int i = 0; i < d.n_atoms; ++i) {
+        if (d.role[i] > 2 || d.type[i] > 1) { why = "role must be 0..2 and type 0..1"; return false; }
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(d.pos[3 * i + a])) { why = "non-finite position"; return false; }
+        if (d.dim == 2 && d.pos[3 * i + 2] != 0.0) { why = "2-D replicas need z == 0"; return false; }
+    }
+    return true;
+}
+
+bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan &P, std::string &why) {
+    if (!reps || n_rep <= 0 || !p) { why = "no replicas or no params"; return false; }
+    if (p->prec != HD_FP64 && p->prec != HD_FP32_SPLIT) { why = "prec must be HD_FP64 or HD_FP32_SPLIT"; return false; }
+    if (!(p->dt > 0.0) || !(p->rc > 0.0) || !(p->skin > 0.0)) { why = "dt, rc and skin must be > 0"; return false; }
+    P.block = p->block > 0 ? p->block : 128;
+    if (P.block % 32 != 0 || P.block > 256) { why = "block must be a multiple of 32, at most 256"; return false; }
+    P.prec = p->prec;
+    P.nrep = n_rep;
+    const double rl = p->rc + p->skin;
+    bool any3 = false;
+    for (int r = 0; r < n_rep; ++r) {
+        if (!valid_desc(reps[r], why)) {
+            why = "replica " + std::to_string(r) + ": " + why;
+            return false;
+        }
+        any3 |= reps[r].dim == 3;
+    }
+    P.maxnb = p->maxnb > 0 ? p->maxnb : (any3 ? 112 : 32);
+    if (P.maxnb > MAXNB_CAP) { why = "maxnb above the build's capacity of 160"; return false; }
+    P.rep.resize(n_rep);
+    int max_occ = 0;
+    long long natom = 0, ntile = 0, ncell = 0;
+    for (int r = 0; r < n_rep; ++r) {
+        const hd_replica_desc &d = reps[r];
+        RepDev R;
+        memset(&R, 0, sizeof R);
+        R.dim = d.dim;
+        R.n = d.n_atoms;
+        R.atom0 = (int)natom;
+        R.tile0 = (int)ntile;
+        R.ntile = (d.n_atoms + P.block - 1) / P.block;
+        R.m_exp = d.m_exp;
+        R.rep_id = d.rep_id;
+        R.vert = d.dim - 1;
+        int nrig = 0;
+        for (int i = 0; i < d.n_atoms; ++i) nrig += d.role[i] == 2;
+        R.nrig = nrig;
+        // geometry, fixed point and cells
+        for (int a = 0; a < 3; ++a) {
+            R.periodic[a] = (a < d.dim && d.periodic[a]) ? 1 : 0;
+            if (R.periodic[a]) {
+                R.L[a] = d.box[a];
+                R.invL[a] = 1.0 / d.box[a];
+                R.fx_scale[a] = 4294967296.0 / d.box[a];
+                R.fx_origin[a] = 0.0;
+                R.fx_lsb[a] = (float)(d.box[a] / 4294967296.0);
+                int nc = (int)std::floor(d.box[a] / (rl * (1.0 + 1e-6)));
+                R.nc[a] = nc >= 3 ? nc : 1;
+            } else if (a < d.dim) {
+                double mn = d.pos[a], mx = d.pos[a];
+                for (int i = 1; i < d.n_atoms; ++i) {
+                    mn = std::min(mn, d.pos[3 * i + a]);
+                    mx = std::max(mx, d.pos[3 * i + a]);
+                }
+                double span = 64.0;
+                while (span < 4.0 * (mx - mn) + 64.0) span *= 2.0;
+                R.fx_origin[a] = 0.5 * (mn + mx);
+                R.fx_scale[a] = 4294967296.0 / span;
+                R.fx_lsb[a] = (float)(span / 4294967296.0);
+                R.open_lim = 0.5 * span - 4.0;
+                const double w = rl * (1.0 + 1e-4), lo = mn - 2.0;
+                R.nc[a] = std::max(1, (int)std::ceil((mx + 2.0 - lo) / w));
+                R.cell_lo_fix = (long long)std::llrint((lo - R.fx_origin[a]) * R.fx_scale[a]);
+                R.cell_inv_w_lsb = (float)((span / 4294967296.0) / w);
+            } else {
+                R.nc[a] = 1;
+            }
+            if (R.nc[a] >= 1024) { why = "replica " + std::to_string(r) + ": more than 1023 cells along an axis"; return false; }
+        }
+        R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
+        R.cell0 = (int)ncell;
+        // occupancy estimate of the initial configuration
+        {
+            std::vector<int> occ(R.ncell, 0);
+            for (int i = 0; i < d.n_atoms; ++i) {
+                int c[3];
+                for (int a = 0; a < 3; ++a) {
+                    if (R.nc[a] == 1) { c[a] = 0; continue; }
+                    double x = d.pos[3 * i + a];
+                    double t;
+                    if (R.periodic[a]) t = (x - R.L[a] * std::floor(x / R.L[a])) / R.L[a] * R.nc[a];
+                    else t = (x - (R.fx_origin[a] + R.cell_lo_fix / R.fx_scale[a])) / (rl * (1.0 + 1e-4));
+                    c[a] = std::min(R.nc[a] - 1, std::max(0, (int)std::floor(t)));
+                }
+                max_occ = std::max(max_occ, ++occ[(c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0]]);
+            }
+        }
+        // interaction constants (Eq. 9 with the shift at rc)
+        R.kT = d.kT;
+        R.beta = 1.0 / d.kT;
+        R.c_ou = std::exp(-d.gamma * p->dt);
+        R.s_ou = std::sqrt((1.0 - R.c_ou * R.c_ou) * d.kT);
+        R.c_ouf = (float)R.c_ou;
+        R.s_ouf = (float)R.s_ou;
+        R.kspring = d.k_spring;
+        R.fnormal = d.f_normal;
+        R.slider[0] = d.slider[0];
+        R.slider[1] = d.slider[1];
+        R.dvmax = d.dvmax;
+        R.sig_lo = d.sig_lo;
+        R.sig_hi = d.sig_hi;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const double eps = d.eps[a][b], sig = d.sig[a][b];
+                const double sc6 = std::pow(sig / p->rc, 6.0);
+                R.eps[a][b] = eps;
+                R.sig2[a][b] = sig * sig;
+                R.shift[a][b] = 4.0 * eps * (sc6 * sc6 - sc6);
+                R.epsf[a][b] = (float)eps;
+                R.sig2f[a][b] = (float)(sig * sig);
+                R.shiftf[a][b] = (float)R.shift[a][b];
+            }
+        R.kr_n = nrig > 0 ? d.k_spring / nrig : 0.0;
+        R.kr_nf = (float)R.kr_n;
+        P.rep[r] = R;
+        for (int k = 0; k < R.ntile; ++k) {
+            P.tile_rep.push_back(r);
+            P.tile_start.push_back(R.atom0 + k * P.block);
+            P.tile_n.push_back(std::min(P.block, d.n_atoms - k * P.block));
+        }
+        natom += d.n_atoms;
+        ntile += R.ntile;
+        ncell += R.ncell;
+        if (natom > (1LL << 30)) { why = "more than 2^30 atoms"; return false; }
+    }
+    P.natom = (int)natom;
+    P.ntile = (int)ntile;
+    P.ncell = (int)ncell;
+    P.cell_cap = p->cell_cap > 0 ? p->cell_cap : ((2 * max_occ + 8 + 7) / 8) * 8;
+    // layout
+    const size_t N = P.natom, T = P.ntile, R = P.nrep;
+    const size_t v4 = P.prec == HD_FP64 ? sizeof(dbl4) : sizeof(float4);
+    size_t cur = 0;
+    P.o_rep = take(cur, R * sizeof(RepDev));
+    P.o_st = take(cur, R * sizeof(RepState));
+    P.o_sc = take(cur, R * sizeof(Scal));
+    P.o_trep = take(cur, T * 4);
+    P.o_tstart = take(cur, T * 4);
+    P.o_tn = take(cur, T * 4);
+    P.o_part = take(cur, T * NPART * 8);
+    P.o_qpart = take(cur, T * NPART * 8);
+    P.o_kpart = take(cur, T * 8);
+    P.o_x = take(cur, N * sizeof(dbl4));
+    P.o_xo = take(cur, N * sizeof(dbl4));
+    P.o_xq = take(cur, N * sizeof(dbl4));
+    P.o_v = take(cur, N * v4);
+    P.o_vq = take(cur, N * v4);
+    P.o_f = take(cur, N * v4);
+    P.o_fq = take(cur, N * v4);
+    P.o_h = take(cur, N * v4);
+    P.o_dr = take(cur, N * v4);
+    P.o_pfix = take(cur, N * 16);
+    P.o_pfixb = take(cur, N * 16);
+    P.o_qpfix = take(cur, N * 16);
+    P.o_qpfixb = take(cur, N * 16);
+    P.o_cellid = take(cur, N * 4);
+    P.o_nnb = take(cur, N * 4);
+    P.o_nbr = take(cur, N * (size_t)P.maxnb * 4);
+    P.o_ccnt = take(cur, (size_t)P.ncell * 4);
+    P.o_catoms = take(cur, (size_t)P.ncell * P.cell_cap * 4);
+    P.o_rebuild = take(cur, R * 4);
+    P.o_qrebuild = take(cur, R * 4);
+    P.o_err = take(cur, 4 * 4);
+    P.o_bar = take(cur, R * 2 * 4);
+    P.o_qdisp = take(cur, R * 8);
+    P.o_drawvel = take(cur, R * 4);
+    P.o_adopt = take(cur, R * 4);
+    P.bytes = (cur + ALIGN - 1) / ALIGN * ALIGN;
+    return true;
+}
+
+}  // namespace
+
+struct hd_ctx {
+    Plan P;
+    Dev D{}, Q{};
+    cudaStream_t s = nullptr;
+    char *ws = nullptr;
+    hd_status status = HD_OK;
+    std::string err;
+    int driver = HD_DRIVER_KERNELS;
+    int persistent_ctas = 0;
+    long long launches = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::vector<double> qdisp;
+    std::vector<int> qflag;
+    long long h2d = 0, d2h = 0;
+    // timing: events recorded around phases; harvested at hd_timing / next step
+    int timing = 0;
+    struct Span { cudaEvent_t a, b; int cat; };
+    std::vector<Span> pending;            // recorded directly on the stream
+    std::map<int, std::vector<Span>> graph_spans;  // event nodes inside graph n
+    std::vector<int> graph_pending;       // graphs launched, spans not yet harvested
+    double tsum[4] = {0, 0, 0, 0};
+    long long tcnt[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> free_events;
+};
+
+namespace {
+
+hd_status fail(hd_ctx *c, hd_status st, const char *fmt, ...) {
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof b, fmt, ap);
+    va_end(ap);
+    if (c && c->status == HD_OK) {
+        c->status = st;
+        c->err = b;
+    }
+    return st;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(c, HD_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                         \
+    } while (0)
+
+template <typename T>
+T *at(char *base, size_t off) { return reinterpret_cast<T *>(base + off); }
+
+enum { T_PAIR = 0, T_UPDATE = 1, T_REBUILD = 2, T_SCALAR = 3 };
+
+cudaEvent_t get_event(hd_ctx *c) {
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Record a start event if timing is on; returns the span index or -1.
+struct Timed {
+    hd_ctx *c;
+    std::vector<hd_ctx::Span> *sink;
+    hd_ctx::Span sp;
+    bool on;
+    Timed(hd_ctx *c_, std::vector<hd_ctx::Span> *sink_, int cat) : c(c_), sink(sink_), on(c_->timing && sink_) {
+        if (on) {
+            sp.a = get_event(c);
+            sp.b = get_event(c);
+            sp.cat = cat;
+            cudaEventRecord(sp.a, c->s);
+        }
+    }
+    ~Timed() {
+        if (on) {
+            cudaEventRecord(sp.b, c->s);
+            sink->push_back(sp);
+        }
+    }
+};
+
+void harvest(hd_ctx *c, std::vector<hd_ctx::Span> &v, bool recycle) {
+    for (auto &sp : v) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+            c->tsum[sp.cat] += ms;
+            c->tcnt[sp.cat] += 1;
+        }
+        if (recycle) {
+            c->free_events.push_back(sp.a);
+            c->free_events.push_back(sp.b);
+        }
+    }
+    if (recycle) v.clear();
+}
+
+void harvest_all(hd_ctx *c) {
+    cudaStreamSynchronize(c->s);
+    harvest(c, c->pending, true);
+    for (int n : c->graph_pending) harvest(c, c->graph_spans[n], false);
+    c->graph_pending.clear();
+}
+
+void fill_dev(hd_ctx *c) {
+    Plan &P = c->P;
+    char *b = c->ws;
+    Dev &D = c->D;
+    D.nrep = P.nrep;
+    D.ntile = P.ntile;
+    D.natom = P.natom;
+    D.maxnb = P.maxnb;
+    D.cell_cap = P.cell_cap;
+    D.ncell = P.ncell;
+    D.prec = P.prec;
+    D.block = P.block;
+    D.rep = at<RepDev>(b, P.o_rep);
+    D.st = at<RepState>(b, P.o_st);
+    D.sc = at<Scal>(b, P.o_sc);
+    D.tile_rep = at<int>(b, P.o_trep);
+    D.tile_start = at<int>(b, P.o_tstart);
+    D.tile_n = at<int>(b, P.o_tn);
+    D.part = at<double>(b, P.o_part);
+    D.kpart = at<double>(b, P.o_kpart);
+    D.x = at<dbl4>(b, P.o_x);
+    D.xo = at<dbl4>(b, P.o_xo);
+    if (P.prec == HD_FP64) {
+        D.v64 = at<dbl4>(b, P.o_v);
+        D.f64 = at<dbl4>(b, P.o_f);
+        D.h64 = at<dbl4>(b, P.o_h);
+        D.dr64 = at<dbl4>(b, P.o_dr);
+    } else {
+        D.v32 = at<float4>(b, P.o_v);
+        D.f32 = at<float4>(b, P.o_f);
+        D.h32 = at<float4>(b, P.o_h);
+        D.dr32 = at<float4>(b, P.o_dr);
+    }
+    D.pfix = at<int4>(b, P.o_pfix);
+    D.pfixb = at<int4>(b, P.o_pfixb);
+    D.cellid = at<int>(b, P.o_cellid);
+    D.nnb = at<int>(b, P.o_nnb);
+    D.nbr = at<int>(b, P.o_nbr);
+    D.cell_cnt = at<int>(b, P.o_ccnt);
+    D.cell_atoms = at<int>(b, P.o_catoms);
+    D.rebuild = at<int>(b, P.o_rebuild);
+    D.err = at<int>(b, P.o_err);
+    D.bar = at<unsigned int>(b, P.o_bar);
+    D.qdisp = at<unsigned long long>(b, P.o_qdisp);
+    // quench view: the copy of the positions and its own velocity, force,
+    // fixed-point image, rebuild flags and tile sums
+    Dev &Q = c->Q;
+    Q = D;
+    Q.x = at<dbl4>(b, P.o_xq);
+    if (P.prec == HD_FP64) {
+        Q.v64 = at<dbl4>(b, P.o_vq);
+        Q.f64 = at<dbl4>(b, P.o_fq);
+    } else {
+        Q.v32 = at<float4>(b, P.o_vq);
+        Q.f32 = at<float4>(b, P.o_fq);
+    }
+    Q.pfix = at<int4>(b, P.o_qpfix);
+    Q.pfixb = at<int4>(b, P.o_qpfixb);
+    Q.rebuild = at<int>(b, P.o_qrebuild);
+    Q.part = at<double>(b, P.o_qpart);
+}
+
+void set_scalars(Dev &D, const hd_params *p) {
+    D.bias_on = p->bias_on ? 1 : 0;
+    D.dt = p->dt;
+    D.rc2 = p->rc * p->rc;
+    const double rl = p->rc + p->skin;
+    D.rl2 = rl * rl;
+    D.half_skin2 = 0.25 * p->skin * p->skin;
+    D.rc2f = (float)D.rc2;
+    D.rl2_lo_f = (float)(D.rl2 * (1.0 - 1.0 / 4096.0));
+    D.rl2_hi_f = (float)(D.rl2 * (1.0 + 1.0 / 4096.0));
+    D.half_skin2_f = (float)(D.half_skin2 * (1.0 - 1e-4));
+    D.seed_lo = (uint32_t)p->seed;
+    D.seed_hi = (uint32_t)(p->seed >> 32);
+}
+
+hd_status check_device(hd_ctx *c) {
+    CK(cudaStreamSynchronize(c->s));
+    CK(cudaGetLastError());
+    int e[4];
+    CK(cudaMemcpy(e, c->D.err, sizeof e, cudaMemcpyDeviceToHost));
+    c->d2h += sizeof e;
+    if (e[0] != 0) {
+        const char *what = e[0] == HD_ERR_OVERFLOW ? "neighbour row or cell over capacity"
+                         : e[0] == HD_ERR_NUMERIC ? "non-finite position or atom outside the open-axis range"
+                         : e[0] == HD_ERR_TIMEOUT ? "device barrier wait ran out"
+                                                  : "device error";
+        return fail(c, (hd_status)e[0], "%s (atom %d, replica %d)", what, e[1], e[2]);
+    }
+    return HD_OK;
+}
+
+hd_status upload_reps(hd_ctx *c) {
+    CK(cudaMemcpyAsync((void *)c->D.rep, c->P.rep.data(), c->P.rep.size() * sizeof(RepDev), cudaMemcpyHostToDevice, c->s));
+    c->h2d += (long long)(c->P.rep.size() * sizeof(RepDev));
+    return HD_OK;
+}
+
+// Kernels of one BAOAB step after the opening half (list, pair, scalars, update).
+void queue_step(hd_ctx *c, int mode, std::vector<hd_ctx::Span> *sink) {
+    { Timed t(c, sink, T_REBUILD); launch_rebuild(c->D, c->s); }
+    { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, c->s); }
+    { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, mode, c->s); }
+    { Timed t(c, sink, T_UPDATE); launch_update(c->D, mode, c->s); }
+    c->launches += 6;
+}
+
+void queue_steps(hd_ctx *c, int n, std::vector<hd_ctx::Span> *sink) {
+    { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, MODE_OPEN, c->s); }
+    { Timed t(c, sink, T_UPDATE); launch_update(c->D, MODE_OPEN, c->s); }
+    c->launches += 2;
+    for (int k = 1; k <= n; ++k) queue_step(c, k < n ? (MODE_CLOSE | MODE_OPEN) : MODE_CLOSE, sink);
+}
+
+hd_status refresh_md(hd_ctx *c, bool relist) {
+    // recompute list (optional), forces, H.dr and scalars at the MD positions
+    if (relist) {
+        std::vector<int> two(c->P.nrep, 2);
+        CK(cudaMemcpyAsync(c->D.rebuild, two.data(), two.size() * 4, cudaMemcpyHostToDevice, c->s));
+        c->h2d += (long long)two.size() * 4;
+        launch_rebuild(c->D, c->s);
+        c->launches += 3;
+        CK(cudaStreamSynchronize(c->s));
+    }
+    launch_pair(c->D, false, c->s);
+    launch_scalar(c->D, 0, c->s);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    return HD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hd_workspace_bytes(const hd_replica_desc *reps, int n_rep, const hd_params *p) {
+    Plan P;
+    std::string why;
+    if (!make_plan(reps, n_rep, p, P, why)) return 0;
+    return P.bytes;
+}
+
+hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, void *d_workspace, size_t ws_bytes,
+                    void *cuda_stream, hd_ctx **out) {
+    if (!out) return HD_ERR_ARG;
+    *out = nullptr;
+    hd_ctx *c = new hd_ctx();
+    *out = c;
+    std::string why;
+    if (!make_plan(reps, n_rep, p, c->P, why)) return fail(c, HD_ERR_ARG, "%s", why.c_str());
+    if (!d_workspace) return fail(c, HD_ERR_ARG, "NULL workspace");
+    if ((uintptr_t)d_workspace % ALIGN) return fail(c, HD_ERR_ARG, "workspace not 256-byte aligned");
+    if (ws_bytes < c->P.bytes)
+        return fail(c, HD_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, c->P.bytes);
+    c->ws = (char *)d_workspace;
+    c->s = (cudaStream_t)cuda_stream;
+    c->driver = (p->driver == HD_DRIVER_PERSISTENT) ? HD_DRIVER_PERSISTENT : HD_DRIVER_KERNELS;
+    fill_dev(c);
+    set_scalars(c->D, p);
+    set_scalars(c->Q, p);
+    Plan &P = c->P;
+    const size_t N = P.natom;
+    CK(cudaMemsetAsync(c->ws, 0, P.bytes, c->s));
+    // host staging
+    std::vector<dbl4> hx(N), hxo(N);
+    std::vector<int4> hp(N);
+    std::vector<char> hv(N * (P.prec == HD_FP64 ? sizeof(dbl4) : sizeof(float4)));
+    std::vector<RepState> hst(P.nrep);
+    std::vector<int> draw(P.nrep), two(P.nrep, 2);
+    memset(hst.data(), 0, hst.size() * sizeof(RepState));
+    for (int r = 0; r < P.nrep; ++r) {
+        const hd_replica_desc &d = reps[r];
+        const int a0 = P.rep[r].atom0;
+        draw[r] = d.vel == nullptr;
+        hst[r].t_h = d.t_h0;
+        hst[r].t_md = d.t_md0;
+        hst[r].step = d.step0;
+        for (int i = 0; i < d.n_atoms; ++i) {
+            const double *x = d.pos + 3 * i;
+            const double *xo = d.pos_ref ? d.pos_ref + 3 * i : x;
+            hx[a0 + i] = make_dbl4(x[0], x[1], x[2], (double)d.type[i]);
+            hxo[a0 + i] = make_dbl4(xo[0], xo[1], xo[2], 0.0);
+            hp[a0 + i] = make_int4(0, 0, 0, (int)d.type[i] | ((int)d.role[i] << 8));
+            double v[3] = {0, 0, 0};
+            if (d.vel && d.role[i] != 0)
+                for (int a = 0; a < 3; ++a) v[a] = d.vel[3 * i + a];
+            if (d.dim == 2) v[2] = 0.0;
+            if (d.vel && d.role[i] == 2) {
+                bool first = true;
+                for (int k = 0; k < i; ++k) first &= d.role[k] != 2;
+                if (first)
+                    for (int a = 0; a < 3; ++a) hst[r].vbody[a] = hst[r].vbody_full[a] = v[a];
+            }
+            if (P.prec == HD_FP64) reinterpret_cast<dbl4 *>(hv.data())[a0 + i] = make_dbl4(v[0], v[1], v[2], 0.0);
+            else reinterpret_cast<float4 *>(hv.data())[a0 + i] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        }
+    }
+    if (upload_reps(c) != HD_OK) return c->status;
+    CK(cudaMemcpyAsync(c->D.st, hst.data(), hst.size() * sizeof(RepState), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync((void *)c->D.tile_rep, P.tile_rep.data(), P.ntile * 4, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync((void *)c->D.tile_start, P.tile_start.data(), P.ntile * 4, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync((void *)c->D.tile_n, P.tile_n.data(), P.ntile * 4, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->D.x, hx.data(), N * sizeof(dbl4), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->D.xo, hxo.data(), N * sizeof(dbl4), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->D.pfix, hp.data(), N * 16, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->ws + P.o_v, hv.data(), hv.size(), cudaMemcpyHostToDevice, c->s));
+    int *d_draw = at<int>(c->ws, P.o_drawvel);
+    CK(cudaMemcpyAsync(d_draw, draw.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->D.rebuild, two.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s));
+    launch_init(c->D, d_draw, c->s);
+    launch_rebuild(c->D, c->s);
+    launch_pair(c->D, false, c->s);
+    launch_scalar(c->D, 0, c->s);
+    launch_update(c->D, MODE_KIN, c->s);  // kinetic energy of the initial velocities
+    launch_obs(c->D, c->s);
+    c->launches += 8;
+    CK(cudaGetLastError());
+    c->qdisp.assign(P.nrep, 0.0);
+    c->qflag.assign(P.nrep, 0);
+    return check_device(c);
+}
+
+hd_status hd_set_slider(hd_ctx *c, const double *slider, int requench_ref) {
+    if (!c) return HD_ERR_ARG;
+    if (c->status != HD_OK) return HD_ERR_STATE;
+    if (!slider) return fail(c, HD_ERR_ARG, "NULL slider array");
+    for (int r = 0; r < c->P.nrep; ++r) {
+        c->P.rep[r].slider[0] = slider[2 * r];
+        c->P.rep[r].slider[1] = slider[2 * r + 1];
+    }
+    // only the two slider words of each replica's settings block move
+    CK(cudaMemcpy2DAsync((char *)c->D.rep + offsetof(RepDev, slider), sizeof(RepDev), &c->P.rep[0].slider[0],
+                         sizeof(RepDev), 2 * sizeof(double), c->P.nrep, cudaMemcpyHostToDevice, c->s));
+    c->h2d += 16LL * c->P.nrep;
+    launch_scalar(c->D, 0, c->s);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    if (requench_ref) return hd_quench(c, 1, 1e-6, 20000, 0.01, 1e300, 2, nullptr);
+    return HD_OK;
+}
+
+hd_status hd_set_bias(hd_ctx *c, const double *bias) {
+    if (!c) return HD_ERR_ARG;
+    if (c->status != HD_OK) return HD_ERR_STATE;
+    if (!bias) return fail(c, HD_ERR_ARG, "NULL bias array");
+    for (int r = 0; r < c->P.nrep; ++r) {
+        if (!(bias[4 * r + 3] >= 1.0)) return fail(c, HD_ERR_ARG, "replica %d: m must be >= 1", r);
+        c->P.rep[r].dvmax = bias[4 * r];
+        c->P.rep[r].sig_lo = bias[4 * r + 1];
+        c->P.rep[r].sig_hi = bias[4 * r + 2];
+        c->P.rep[r].m_exp = (int)bias[4 * r + 3];
+    }
+    if (upload_reps(c) != HD_OK) return c->status;
+    launch_scalar(c->D, 0, c->s);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    return HD_OK;
+}
+
+hd_status hd_step(hd_ctx *c, int n_steps) {
+    if (!c) return HD_ERR_ARG;
+    if (c->status != HD_OK) return HD_ERR_STATE;
+    if (n_steps < 0) return fail(c, HD_ERR_ARG, "n_steps < 0");
+    if (n_steps == 0) return HD_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(c->s, &cs));
+    const bool can_graph = c->s != nullptr && cs == cudaStreamCaptureStatusNone;
+    if (c->timing && !c->graph_pending.empty()) harvest_all(c);
+    if (!can_graph) {
+        queue_steps(c, n_steps, &c->pending);
+        CK(cudaGetLastError());
+        return HD_OK;
+    }
+    const int key = c->timing ? -n_steps : n_steps;
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        if (c->graphs.size() >= 8) {
+            harvest_all(c);
+            for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+            c->graphs.clear();
+            for (auto &kv : c->graph_spans)
+                for (auto &sp : kv.second) {
+                    c->free_events.push_back(sp.a);
+                    c->free_events.push_back(sp.b);
+                }
+            c->graph_spans.clear();
+        }
+        cudaGraph_t g;
+        long long before = c->launches;
+        std::vector<hd_ctx::Span> spans;
+        CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+        queue_steps(c, n_steps, c->timing ? &spans : nullptr);
+        CK(cudaStreamEndCapture(c->s, &g));
+        c->launches = before;
+        cudaGraphExec_t ge;
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        cudaGraphDestroy(g);
+        it = c->graphs.emplace(key, ge).first;
+        if (c->timing) c->graph_spans[key] = spans;
+    }
+    CK(cudaGraphLaunch(it->second, c->s));
+    if (c->timing) c->graph_pending.push_back(key);
+    c->launches += 2 + 6LL * n_steps;
+    return HD_OK;
+}
+
+hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double step_size, double theta, int adopt,
+                    int32_t *h_flags) {
+    if (!c) return HD_ERR_ARG;
+    if (c->status != HD_OK) return HD_ERR_STATE;
+    if ((method != 0 && method != 1) || !(ftol > 0.0) || max_iter < 0 || !(step_size > 0.0) || adopt < 0 || adopt > 2)
+        return fail(c, HD_ERR_ARG, "bad quench arguments");
+    Dev &Q = c->Q;
+    Q.q_method = method;
+    Q.q_ftol = ftol;
+    Q.q_step = step_size;
+    Q.q_theta = theta;
+    const int R = c->P.nrep;
+    launch_qinit(Q, c->D, c->s);
+    c->launches += 1;
+    std::vector<RepState> st(R);
+    const int chunk = 32;
+    for (int done_iters = 0; done_iters <= max_iter;) {
+        for (int k = 0; k < chunk; ++k) launch_qiter(Q, max_iter, c->s);
+        c->launches += 6LL * chunk;
+        done_iters += chunk;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(st.data(), c->D.st, R * sizeof(RepState), cudaMemcpyDeviceToHost, c->s));
+        c->d2h += (long long)(R * sizeof(RepState));
+        CK(cudaStreamSynchronize(c->s));
+        bool all = true;
+        for (int r = 0; r < R; ++r) all &= st[r].q_done != 0;
+        if (all) break;
+    }
+    launch_qdisp(Q, c->s);
+    c->launches += 1;
+    std::vector<unsigned long long> qd(R);
+    CK(cudaMemcpyAsync(qd.data(), c->D.qdisp, R * 8, cudaMemcpyDeviceToHost, c->s));
+    c->d2h += 8LL * R;
+    CK(cudaStreamSynchronize(c->s));
+    std::vector<int> ad(R);
+    bool any = false;
+    for (int r = 0; r < R; ++r) {
+        double m;
+        memcpy(&m, &qd[r], 8);
+        c->qdisp[r] = std::sqrt(m);
+        c->qflag[r] = std::sqrt(m) > theta;
+        if (h_flags) h_flags[r] = c->qflag[r];
+        ad[r] = adopt == 2 || (adopt == 1 && c->qflag[r]);
+        any |= ad[r] != 0;
+    }
+    if (any) {
+        int *d_ad = at<int>(c->ws, c->P.o_adopt);
+        CK(cudaMemcpyAsync(d_ad, ad.data(), R * 4, cudaMemcpyHostToDevice, c->s));
+        c->h2d += 4LL * R;
+        launch_adopt(Q, c->D, d_ad, c->s);
+        c->launches += 1;
+    }
+    if (refresh_md(c, true) != HD_OK) return c->status;
+    return check_device(c);
+}
+
+hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) {
+    if (!c) return HD_ERR_ARG;
+    if (!h_dst) return fail(c, HD_ERR_ARG, "NULL destination");
+    const Plan &P = c->P;
+    if (field == HD_FIELD_OBS && replica == -1) {
+        if (bytes != (size_t)P.nrep * HD_OBS_LEN * 8) return fail(c, HD_ERR_ARG, "OBS: %zu bytes expected", (size_t)P.nrep * HD_OBS_LEN * 8);
+        for (int r = 0; r < P.nrep; ++r) {
+            hd_status s = hd_read(c, field, r, (char *)h_dst + (size_t)r * HD_OBS_LEN * 8, HD_OBS_LEN * 8);
+            if (s != HD_OK) return s;
+        }
+        return HD_OK;
+    }
+    if (replica < 0 || replica >= P.nrep) return fail(c, HD_ERR_ARG, "replica %d out of range", replica);
+    if (c->status == HD_OK) {
+        if (field == HD_FIELD_OBS) {
+            launch_obs(c->D, c->s);
+            c->launches += 1;
+        }
+        check_device(c);
+    }
+    const RepDev &R = P.rep[replica];
+    const size_t n = R.n, a0 = R.atom0;
+    auto need = [&](size_t b) { return bytes == b; };
+    auto vec3 = [&](const void *dptr, bool fp64, int comp_w) -> hd_status {
+        // comp_w < 0: xyz into [n][3]; comp_w = 3: the w component into [n]
+        const size_t es = fp64 ? sizeof(dbl4) : sizeof(float4);
+        std::vector<char> buf(n * es);
+        CK(cudaMemcpy(buf.data(), (const char *)dptr + a0 * es, n * es, cudaMemcpyDeviceToHost));
+        c->d2h += (long long)(n * es);
+        double *o = (double *)h_dst;
+        for (size_t i = 0; i < n; ++i) {
+            double q[4];
+            if (fp64) {
+                const dbl4 v = reinterpret_cast<const dbl4 *>(buf.data())[i];
+                q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+            } else {
+                const float4 v = reinterpret_cast<const float4 *>(buf.data())[i];
+                q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+            }
+            if (comp_w == 3) o[i] = q[3];
+            else for (int a = 0; a < 3; ++a) o[3 * i + a] = q[a];
+        }
+        return HD_OK;
+    };
+    const bool f64 = P.prec == HD_FP64;
+    switch (field) {
+    case HD_FIELD_POS:
+        if (!need(n * 24)) break;
+        return vec3(c->D.x, true, -1);
+    case HD_FIELD_REF:
+        if (!need(n * 24)) break;
+        return vec3(c->D.xo, true, -1);
+    case HD_FIELD_QPOS:
+        if (!need(n * 24)) break;
+        return vec3(c->Q.x, true, -1);
+    case HD_FIELD_VEL:
+        if (!need(n * 24)) break;
+        return vec3(c->ws + P.o_v, f64, -1);
+    case HD_FIELD_FORCE:
+        if (!need(n * 24)) break;
+        return vec3(c->ws + P.o_f, f64, -1);
+    case HD_FIELD_ENERGY:
+        if (!need(n * 8)) break;
+        return vec3(c->ws + P.o_f, f64, 3);
+    case HD_FIELD_HDR:
+        if (!need(n * 24)) break;
+        return vec3(c->ws + P.o_h, f64, -1);
+    case HD_FIELD_NBR_COUNT:
+        if (!need(n * 4)) break;
+        CK(cudaMemcpy(h_dst, c->D.nnb + a0, n * 4, cudaMemcpyDeviceToHost));
+        c->d2h += 4LL * n;
+        return HD_OK;
+    case HD_FIELD_CELL:
+        if (!need(n * 4)) break;
+        CK(cudaMemcpy(h_dst, c->D.cellid + a0, n * 4, cudaMemcpyDeviceToHost));
+        c->d2h += 4LL * n;
+        return HD_OK;
+    case HD_FIELD_NBR: {
+        if (!need(n * P.maxnb * 4)) break;
+        std::vector<int> cnt(n), slab(n * P.maxnb);
+        CK(cudaMemcpy(cnt.data(), c->D.nnb + a0, n * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy2D(slab.data(), n * 4, c->D.nbr + a0, (size_t)P.natom * 4, n * 4, P.maxnb, cudaMemcpyDeviceToHost));
+        c->d2h += 4LL * n * (1 + P.maxnb);
+        int *o = (int *)h_dst;
+        for (size_t i = 0; i < n; ++i)
+            for (int k = 0; k < P.maxnb; ++k) o[i * P.maxnb + k] = k < cnt[i] ? slab[(size_t)k * n + i] - (int)a0 : -1;
+        return HD_OK;
+    }
+    case HD_FIELD_OBS: {
+        if (!need(HD_OBS_LEN * 8)) break;
+        RepState S;
+        Scal C;
+        CK(cudaMemcpy(&S, c->D.st + replica, sizeof S, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&C, c->D.sc + replica, sizeof C, cudaMemcpyDeviceToHost));
+        c->d2h += (long long)(sizeof S + sizeof C);
+        double *o = (double *)h_dst;
+        memset(o, 0, HD_OBS_LEN * 8);
+        o[HD_OBS_STEP] = (double)S.step;
+        o[HD_OBS_TMD] = S.t_md;
+        o[HD_OBS_TH] = S.t_h;
+        o[HD_OBS_V] = C.V;
+        o[HD_OBS_K] = S.K;
+        o[HD_OBS_DV] = C.dV;
+        o[HD_OBS_SIGMA] = C.sigma;
+        o[HD_OBS_D] = C.d;
+        o[HD_OBS_FR] = C.FR;
+        o[HD_OBS_XT] = C.xT[0];
+        o[HD_OBS_YT] = C.xT[1];
+        o[HD_OBS_ZT] = C.xT[2];
+        o[HD_OBS_NREBUILD] = (double)S.n_rebuild;
+        o[HD_OBS_BOOST] = std::exp(C.dV / R.kT);
+        o[HD_OBS_QITER] = S.q_iter;
+        o[HD_OBS_QFMAX] = S.q_fmax;
+        o[HD_OBS_G] = C.G;
+        for (int a = 0; a < 3; ++a) {
+            o[HD_OBS_FBODY + a] = C.fbody[a];
+            o[HD_OBS_VBODY + a] = S.vbody_full[a];
+        }
+        o[HD_OBS_QDISP] = c->qdisp.empty() ? 0.0 : c->qdisp[replica];
+        return HD_OK;
+    }
+    default:
+        return fail(c, HD_ERR_ARG, "unknown field %d", field);
+    }
+    return fail(c, HD_ERR_ARG, "field %d of replica %d: wrong byte count %zu", field, replica, bytes);
+}
+
+hd_status hd_info(const hd_ctx *c, int64_t out[12]) {
+    if (!c || !out) return HD_ERR_ARG;
+    out[8] = c->h2d;
+    out[9] = c->d2h;
+    out[10] = (int64_t)c->P.bytes;
+    out[11] = 0;
+    out[0] = c->P.nrep;
+    out[1] = c->P.natom;
+    out[2] = c->P.maxnb;
+    out[3] = c->P.cell_cap;
+    out[4] = c->P.ntile;
+    out[5] = c->driver;
+    out[6] = c->persistent_ctas;
+    out[7] = c->launches;
+    return HD_OK;
+}
+
+hd_status hd_sync(hd_ctx *c) {
+    if (!c) return HD_ERR_ARG;
+    if (c->status != HD_OK) return HD_ERR_STATE;
+    return check_device(c);
+}
+
+hd_status hd_timing(hd_ctx *c, int enable, double out[8]) {
+    if (!c) return HD_ERR_ARG;
+    if (enable < -1 || enable > 2) return fail(c, HD_ERR_ARG, "timing mode %d", enable);
+    harvest_all(c);
+    if (enable == 2) {
+        for (int k = 0; k < 4; ++k) { c->tsum[k] = 0.0; c->tcnt[k] = 0; }
+    } else if (enable >= 0) {
+        c->timing = enable;
+    }
+    if (out)
+        for (int k = 0; k < 4; ++k) {
+            out[2 * k] = c->tsum[k];
+            out[2 * k + 1] = (double)c->tcnt[k];
+        }
+    return HD_OK;
+}
+
+void hd_destroy(hd_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->s);
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    for (auto &sp : c->pending) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+    for (auto &kv : c->graph_spans)
+        for (auto &sp : kv.second) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+    for (auto e : c->free_events) cudaEventDestroy(e);
+    delete c;
+}
+
+const char *hd_last_error(const hd_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+}  // extern "C"

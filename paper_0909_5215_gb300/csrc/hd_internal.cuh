@@ -1,0 +1,222 @@
+// hd_internal.cuh -- device-side data layout and helpers of libhdslide.
+//
+// Layout in HBM (one caller-owned workspace, 256-byte aligned blocks):
+//   per atom, all replicas back to back (atom g of replica r at atom0[r] + local):
+//     x      dbl4  FP64 position, w = LJ type           (never wrapped)
+//     xo     dbl4  basin minimum r_O
+//     v      dbl4 (FP64 form) | float4 (split form)    velocity
+//     f      dbl4 | float4   LJ force, w = per-atom energy (half of each pair)
+//     h      dbl4 | float4   H.(r - r_O), spring term included
+//     dr     dbl4 | float4   r - r_O
+//     pfix   int4     32-bit fixed-point position, w = type | role << 8
+//     pfixb  int4     pfix at the last list build (displacement check)
+//     nbr    int32 [maxnb][natom] column-major Verlet list (global j), nnb int32
+//   per cell: count int32, atoms int32 [cell_cap]
+//   per tile (block atoms of one replica): NPART FP64 partial sums, FP64 K part
+//   per replica: RepDev (settings), RepState (clocks, body), Scal (scalars)
+//
+// Fixed point: on a periodic axis x_fix = rint(x * 2^32 / L) taken modulo 2^32,
+// so the int32 difference of two atoms is the minimum image exactly; on the
+// open axis x_fix = rint((x - origin) * 2^32 / span) with |x - origin| kept
+// below span / 2 - 4 (checked every step).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hd.h"
+
+namespace hd {
+
+// 32-byte aligned FP64 quadruple (one 256-bit access per atom)
+typedef double4_32a dbl4;
+__host__ __device__ __forceinline__ dbl4 make_dbl4(double x, double y, double z, double w) {
+    return make_double4_32a(x, y, z, w);
+}
+
+constexpr int NPART = 16;        // per-tile partial sums (see PART_*)
+constexpr int MAXNB_CAP = 160;   // largest neighbour-row capacity a build supports
+constexpr int QPART = 12;        // per-tile partial sums of the quench
+
+enum {
+    PART_D2 = 0, PART_G = 1, PART_V = 2, PART_FRIG = 3, PART_HRIG = 6, PART_DRRIG = 9,
+    PART_XRIG = 12, PART_PAD = 15
+};
+enum { QP_FMAX2 = 0, QP_P = 1, QP_VV = 2, QP_FF = 3, QP_FRIG = 4, QP_XRIG = 7, QP_PAD = 10 };
+
+enum { MODE_CLOSE = 1, MODE_OPEN = 2, MODE_KIN = 4 };  // KIN: kinetic energy only
+enum { ROLE_FIXED = 0, ROLE_MOBILE = 1, ROLE_RIGID = 2 };
+
+struct RepDev {
+    int dim, n, atom0, tile0, ntile, nrig, m_exp, rep_id;
+    int cell0, ncell, vert, pad0;
+    int nc[3], periodic[3];
+    double L[3], invL[3];
+    double kT, beta, c_ou, s_ou, kspring, fnormal, slider[2];
+    double dvmax, sig_lo, sig_hi;
+    double eps[2][2], sig2[2][2], shift[2][2];
+    float epsf[2][2], sig2f[2][2], shiftf[2][2];
+    double fx_scale[3], fx_origin[3];
+    float fx_lsb[3];
+    float cell_inv_w_lsb;        // open axis: cells per fixed-point unit
+    long long cell_lo_fix;       // open axis: fixed-point origin of the cell grid
+    double open_lim;             // escape bound |x - origin| on the open axis
+    double kr_n;                 // k / n_rig (spring Hessian per rigid atom)
+    float kr_nf, c_ouf, s_ouf, pad1;
+};
+
+struct RepState {
+    double t_h, t_md, vbody[3], vbody_full[3], K;
+    long long step, n_rebuild;
+    // quench
+    double q_dt, q_alpha, q_vb[3], q_fmax, q_disp;
+    int q_npos, q_iter, q_done, q_flag;
+};
+
+struct Scal {
+    double d, sigma, dV, dVp, G, V, Vlj, xT[3], fbody[3], FR;
+    double ca, cb;
+    double vb_mid[3], vb_new[3];
+    long long step_cur;
+    // quench scalars of the current iteration
+    double q_fbody[3], q_mix, q_alpha, q_dt, q_vb[3];
+    int q_zero, q_active;
+};
+
+struct Dev {
+    int nrep, ntile, natom, maxnb, cell_cap, ncell, prec, bias_on, block;
+    int q_method, pad0;
+    double dt, rc2, rl2, half_skin2, q_ftol, q_step, q_theta;
+    float rc2f, rl2_lo_f, rl2_hi_f, half_skin2_f;
+    uint32_t seed_lo, seed_hi;
+    const RepDev *rep;
+    RepState *st;
+    Scal *sc;
+    const int *tile_rep, *tile_start, *tile_n;
+    double *part, *kpart;
+    dbl4 *x, *xo;
+    dbl4 *v64, *f64, *h64, *dr64;
+    float4 *v32, *f32, *h32, *dr32;
+    int4 *pfix, *pfixb;
+    int *cellid, *nnb, *nbr, *cell_cnt, *cell_atoms;
+    int *rebuild;                // per replica: list rebuild requested
+    int *err;                    // [0] first error code, [1] atom, [2] replica
+    unsigned int *bar;           // per replica barrier counters (persistent driver)
+    unsigned long long *qdisp;   // per replica max |x_q - r_O|^2 (bits of the double)
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ void set_err(const Dev &D, int code, int atom, int rep) {
+    if (atomicCAS(D.err, 0, code) == 0) {
+        D.err[1] = atom;
+        D.err[2] = rep;
+    }
+}
+
+// Philox4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_draw(const Dev &D, long long step, int atom, int rep_id, int call) {
+    uint4 c = make_uint4((uint32_t)(unsigned long long)step, (uint32_t)atom, (uint32_t)rep_id,
+                         (uint32_t)call | ((uint32_t)((unsigned long long)step >> 32) << 8));
+    return philox10(c, D.seed_lo, D.seed_hi);
+}
+
+// (k + 1/2) 2^-52 with k = (a>>6) 2^26 + (b>>6): strictly inside (0,1), exact in FP64.
+__device__ __forceinline__ double unif64(uint32_t a, uint32_t b) {
+    return ((double)(a >> 6) * 67108864.0 + (double)(b >> 6) + 0.5) * 0x1p-52;
+}
+// FP32 rounding of the same uniform, with full relative precision near 0.
+__device__ __forceinline__ float unif32(uint32_t a, uint32_t b) {
+    return fmaf((float)(a >> 6), 0x1p-26f, ((float)(b >> 6) + 0.5f) * 0x1p-52f);
+}
+
+__device__ __forceinline__ void normals64(uint4 w, double &n0, double &n1) {
+    double u1 = unif64(w.x, w.y), u2 = unif64(w.z, w.w);
+    double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    n0 = rad * c;
+    n1 = rad * s;
+}
+__device__ __forceinline__ void normals32(uint4 w, float &n0, float &n1) {
+    float u1 = unif32(w.x, w.y), u2 = unif32(w.z, w.w);
+    float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    n0 = rad * c;
+    n1 = rad * s;
+}
+
+// Fixed-point image of one coordinate.
+__device__ __forceinline__ int fix_coord(const RepDev &R, int a, double x) {
+    if (R.fx_scale[a] == 0.0) return 0;
+    long long q = __double2ll_rn((x - R.fx_origin[a]) * R.fx_scale[a]);
+    return (int)(unsigned int)(unsigned long long)q;
+}
+
+__device__ __forceinline__ int4 fix_pos(const RepDev &R, dbl4 x, int w) {
+    return make_int4(fix_coord(R, 0, x.x), fix_coord(R, 1, x.y), fix_coord(R, 2, x.z), w);
+}
+
+// Cell of a fixed-point position: exact integer map on periodic axes,
+// clamped linear map on the open axis.
+__device__ __forceinline__ int cell_axis(const RepDev &R, int a, int q) {
+    int nc = R.nc[a];
+    if (nc <= 1) return 0;
+    if (R.periodic[a]) return (int)(((unsigned long long)(unsigned int)q * (unsigned long long)nc) >> 32);
+    float t = (float)((long long)q - R.cell_lo_fix) * R.cell_inv_w_lsb;
+    int c = (int)floorf(t);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// The oracle's squared distance, op for op: minimum image per axis as
+// d - L rint(d / L), then ((dx dx + dy dy) + dz dz), every operation rounded.
+__device__ __forceinline__ double exact_r2(const RepDev &R, dbl4 a, dbl4 b) {
+    double d0 = __dsub_rn(a.x, b.x), d1 = __dsub_rn(a.y, b.y), d2 = __dsub_rn(a.z, b.z);
+    if (R.periodic[0]) d0 = __dsub_rn(d0, __dmul_rn(R.L[0], rint(__ddiv_rn(d0, R.L[0]))));
+    if (R.periodic[1]) d1 = __dsub_rn(d1, __dmul_rn(R.L[1], rint(__ddiv_rn(d1, R.L[1]))));
+    if (R.periodic[2]) d2 = __dsub_rn(d2, __dmul_rn(R.L[2], rint(__ddiv_rn(d2, R.L[2]))));
+    return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+}
+
+__device__ __forceinline__ double mi64(const RepDev &R, int a, double d) {
+    return R.periodic[a] ? d - R.L[a] * rint(d * R.invL[a]) : d;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Eq. 14: value and derivative of DeltaV_1(sigma).
+__device__ __forceinline__ void dv1(const RepDev &R, double s, double &dv, double &dvp) {
+    if (s >= R.sig_hi) { dv = R.dvmax; dvp = 0.0; return; }
+    if (s <= R.sig_lo) { dv = 0.0; dvp = 0.0; return; }
+    double t = (s - R.sig_hi) / (R.sig_lo - R.sig_hi);
+    double tm1 = 1.0;
+    for (int k = 1; k < R.m_exp; ++k) tm1 *= t;
+    double q = 1.0 - tm1 * t;
+    dv = R.dvmax * q * q;
+    dvp = 2.0 * R.dvmax * q * (-(double)R.m_exp * tm1) / (R.sig_lo - R.sig_hi);
+}
+
+}  // namespace hd

@@ -1,0 +1,862 @@
+// hd_kernels.cu -- per-phase kernels of libhdslide (sm_103a).
+//
+// One step of the batched path, per replica (Kim & Falk, Sec. 2.2-2.3):
+//   [k_cell_clear, k_bin, k_nlist]  Verlet list rebuild, only for replicas
+//                                   whose rebuild flag is set
+//   k_pair{64,32}                   LJ force + energy (Eq. 9) and H.(r - r_O)
+//                                   in one sweep of the list; per-tile sums
+//   k_scalar                        per replica: d (Eq. 7), sigma (Eq. 5),
+//                                   DeltaV_1 (Eq. 14), rigid-body force, clocks
+//   k_update{64,32}                 bias force + BAOAB kicks/drifts/noise
+// The quench (steepest descent / FIRE) reuses the list and pair kernels on a
+// copy of the positions (k_pair<true>, k_qscalar, k_qupdate).
+//
+// Tiles: a CTA handles one tile = up to blockDim atoms of ONE replica, so any
+// per-replica quantity is a fixed-order sum of per-tile sums (deterministic).
+#include "hd_internal.cuh"
+#include "hd_launch.h"
+
+namespace hd {
+
+// ---------------------------------------------------------------- reductions
+// Sums NV per-thread values over the CTA in a fixed order and writes them to
+// out[0..NV).  Slot `maxslot` (if >= 0) is reduced with max instead of +.
+template <int NV>
+__device__ __forceinline__ void cta_reduce(double (&v)[NV], double *out, int maxslot) {
+    __shared__ double sm[32][NV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = (q == maxslot) ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sm[w][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int q = threadIdx.x;
+        double a = sm[0][q];
+        for (int k = 1; k < nw; ++k) a = (q == maxslot) ? fmax(a, sm[k][q]) : a + sm[k][q];
+        out[q] = a;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- init
+// Fixed-point image, r - r_O, and (where asked) Maxwell-Boltzmann velocities
+// from Philox calls 2 and 3 at the current step.
+__global__ void k_init(Dev D, const int *draw_vel) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    if (threadIdx.x >= D.tile_n[t]) return;
+    const int i = D.tile_start[t] + threadIdx.x;
+    const RepDev &R = D.rep[r];
+    dbl4 x = D.x[i], xo = D.xo[i];
+    int4 p = D.pfix[i];  // w (type | role << 8) preset by the host
+    p = fix_pos(R, x, p.w);
+    D.pfix[i] = p;
+    D.pfixb[i] = p;
+    const int role = (p.w >> 8) & 0xff;
+    if (D.prec == HD_FP64)
+        D.dr64[i] = make_dbl4(x.x - xo.x, x.y - xo.y, x.z - xo.z, 0.0);
+    else
+        D.dr32[i] = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
+    if (draw_vel[r]) {
+        double v0 = 0, v1 = 0, v2 = 0;
+        if (role == ROLE_MOBILE) {
+            const double sd = sqrt(R.kT);
+            double z0, z1, z2, z3;
+            normals64(philox_draw(D, D.st[r].step, i - R.atom0, R.rep_id, 2), z0, z1);
+            v0 = sd * z0;
+            v1 = sd * z1;
+            if (R.dim == 3) {
+                normals64(philox_draw(D, D.st[r].step, i - R.atom0, R.rep_id, 3), z2, z3);
+                v2 = sd * z2;
+            }
+        }
+        if (D.prec == HD_FP64) D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
+        else D.v32[i] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------- neighbour list
+__global__ void k_cell_clear(Dev D) {
+    const int r = blockIdx.x;
+    if (!D.rebuild[r]) return;
+    const RepDev &R = D.rep[r];
+    for (int c = threadIdx.x; c < R.ncell; c += blockDim.x) D.cell_cnt[R.cell0 + c] = 0;
+}
+
+__global__ void k_bin(Dev D) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
+    const int i = D.tile_start[t] + threadIdx.x;
+    const RepDev &R = D.rep[r];
+    const int4 p = D.pfix[i];
+    const int cx = cell_axis(R, 0, p.x), cy = cell_axis(R, 1, p.y), cz = cell_axis(R, 2, p.z);
+    D.cellid[i] = cx | (cy << 10) | (cz << 20);
+    const int c = R.cell0 + (cz * R.nc[1] + cy) * R.nc[0] + cx;
+    const int slot = atomicAdd(&D.cell_cnt[c], 1);
+    if (slot < D.cell_cap) D.cell_atoms[(size_t)c * D.cell_cap + slot] = i;
+    else set_err(D, HD_ERR_OVERFLOW, i, r);
+    D.pfixb[i] = p;
+}
+
+// Row i = every j != i whose FP64 minimum-image squared distance is below
+// (rc + skin)^2, ascending in j.  Candidates come from the 27 (9 in 2-D)
+// surrounding cells; an FP32 test on the exact integer differences decides
+// all but a thin band around the radius, where the FP64 test of the oracle
+// is repeated operation for operation.
+__global__ void __launch_bounds__(128) k_nlist(Dev D) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
+    const int i = D.tile_start[t] + threadIdx.x;
+    const RepDev &R = D.rep[r];
+    const int4 pi = D.pfix[i];
+    const dbl4 xi = D.x[i];
+    const int cid = D.cellid[i];
+    const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
+    int cs[3][3], ncs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int nc = R.nc[a];
+        ncs[a] = 0;
+        if (nc == 1) {
+            cs[a][ncs[a]++] = 0;
+        } else {
+            for (int d = -1; d <= 1; ++d) {
+                int c = ci[a] + d;
+                if (R.periodic[a]) c = (c + nc) % nc;
+                else if (c < 0 || c >= nc) continue;
+                cs[a][ncs[a]++] = c;
+            }
+        }
+    }
+    const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
+    int row[MAXNB_CAP];
+    int cnt = 0;
+    bool over = false;
+    const int cap = D.maxnb;
+    for (int iz = 0; iz < ncs[2]; ++iz)
+        for (int iy = 0; iy < ncs[1]; ++iy)
+            for (int ix = 0; ix < ncs[0]; ++ix) {
+                const int c = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
+                const int m = min(D.cell_cnt[c], D.cell_cap);
+                const int *ca = D.cell_atoms + (size_t)c * D.cell_cap;
+                for (int k = 0; k < m; ++k) {
+                    const int j = ca[k];
+                    if (j == i) continue;
+                    const int4 pj = D.pfix[j];
+                    const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
+                    const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
+                    const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    bool in;
+                    if (r2 < D.rl2_lo_f) in = true;
+                    else if (r2 >= D.rl2_hi_f) in = false;
+                    else in = exact_r2(R, xi, D.x[j]) < D.rl2;
+                    if (!in) continue;
+                    if (cnt < cap) {
+                        int q = cnt;
+                        while (q > 0 && row[q - 1] > j) {
+                            row[q] = row[q - 1];
+                            --q;
+                        }
+                        row[q] = j;
+                        ++cnt;
+                    } else {
+                        over = true;
+                    }
+                }
+            }
+    for (int k = 0; k < cnt; ++k) D.nbr[(size_t)k * D.natom + i] = row[k];
+    D.nnb[i] = cnt;
+    if (over) set_err(D, HD_ERR_OVERFLOW, i, r);
+}
+
+// ---------------------------------------------------------------- pair sweep
+// F_i = sum_j -phi'(r)/r r_ij; e_i = sum_j phi(r)/2;
+// (H dr)_i = sum_j [A (dr_i - dr_j) + B ((dr_i - dr_j) . r_ij) r_ij],
+// A = phi'/r, B = (phi'' - phi'/r)/r^2, with s = sigma_ab/r:
+//   -A = 24 eps s^6 (2 s^6 - 1)/r^2,   B = 96 eps s^6 (7 s^6 - 2)/r^4.
+// Q (quench): positions of the quench copy, no H.dr, quench partial sums.
+template <bool Q>
+__global__ void __launch_bounds__(256) k_pair64(Dev D) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    if (Q && D.st[r].q_done) return;
+    const RepDev &R = D.rep[r];
+    const bool act = threadIdx.x < D.tile_n[t];
+    const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
+    const dbl4 xi = D.x[i];
+    const int ti = (int)xi.w;
+    const dbl4 dri = Q ? make_dbl4(0, 0, 0, 0) : D.dr64[i];
+    double fx = 0, fy = 0, fz = 0, e = 0, hx = 0, hy = 0, hz = 0;
+    const int nn = act ? D.nnb[i] : 0;
+    const double rc2 = D.rc2;
+    for (int k = 0; k < nn; ++k) {
+        const int j = D.nbr[(size_t)k * D.natom + i];
+        const dbl4 xj = D.x[j];
+        const double dx = mi64(R, 0, xi.x - xj.x), dy = mi64(R, 1, xi.y - xj.y), dz = mi64(R, 2, xi.z - xj.z);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rc2) {
+            const int tj = (int)xj.w;
+            const double eps = R.eps[ti][tj];
+            const double ir2 = 1.0 / r2;
+            const double s2 = R.sig2[ti][tj] * ir2;
+            const double s6 = s2 * s2 * s2;
+            const double fr = 24.0 * eps * ir2 * s6 * (2.0 * s6 - 1.0);
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            e += 0.5 * (4.0 * eps * s6 * (s6 - 1.0) - R.shift[ti][tj]);
+            if (!Q) {
+                const dbl4 drj = D.dr64[j];
+                const double ux = dri.x - drj.x, uy = dri.y - drj.y, uz = dri.z - drj.z;
+                const double rdu = dx * ux + dy * uy + dz * uz;
+                const double B = 96.0 * eps * ir2 * ir2 * s6 * (7.0 * s6 - 2.0);
+                hx += -fr * ux + B * rdu * dx;
+                hy += -fr * uy + B * rdu * dy;
+                hz += -fr * uz + B * rdu * dz;
+            }
+        }
+    }
+    const int role = act ? ((D.pfix[i].w >> 8) & 0xff) : -1;
+    if (!Q && role == ROLE_RIGID) {
+        hx += R.kr_n * dri.x;
+        if (R.dim == 3) hy += R.kr_n * dri.y;
+    }
+    if (act) {
+        D.f64[i] = make_dbl4(fx, fy, fz, e);
+        if (!Q) D.h64[i] = make_dbl4(hx, hy, hz, 0.0);
+    }
+    const bool rig = role == ROLE_RIGID;
+    if (!Q) {
+        double v[NPART] = {};
+        if (act) {
+            v[PART_D2] = dri.x * dri.x + dri.y * dri.y + dri.z * dri.z;
+            v[PART_G] = -(fx * dri.x + fy * dri.y + fz * dri.z);
+            v[PART_V] = e;
+        }
+        if (rig) {
+            v[PART_FRIG] = fx; v[PART_FRIG + 1] = fy; v[PART_FRIG + 2] = fz;
+            v[PART_HRIG] = hx; v[PART_HRIG + 1] = hy; v[PART_HRIG + 2] = hz;
+            v[PART_DRRIG] = dri.x; v[PART_DRRIG + 1] = dri.y; v[PART_DRRIG + 2] = dri.z;
+            v[PART_XRIG] = xi.x; v[PART_XRIG + 1] = xi.y; v[PART_XRIG + 2] = xi.z;
+        }
+        cta_reduce<NPART>(v, D.part + (size_t)t * NPART, -1);
+    } else {
+        double v[QPART] = {};
+        if (role == ROLE_MOBILE) {
+            const dbl4 vv = D.v64[i];
+            v[QP_FMAX2] = fx * fx + fy * fy + fz * fz;
+            v[QP_P] = fx * vv.x + fy * vv.y + fz * vv.z;
+            v[QP_VV] = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
+            v[QP_FF] = v[QP_FMAX2];
+        }
+        if (rig) {
+            v[QP_FRIG] = fx; v[QP_FRIG + 1] = fy; v[QP_FRIG + 2] = fz;
+            v[QP_XRIG] = xi.x; v[QP_XRIG + 1] = xi.y; v[QP_XRIG + 2] = xi.z;
+        }
+        cta_reduce<QPART>(v, D.part + (size_t)t * NPART, QP_FMAX2);
+    }
+}
+
+// Split form: positions are differenced exactly in 32-bit fixed point, the
+// pair arithmetic is FP32; per-tile sums are carried in FP64.
+template <bool Q>
+__global__ void __launch_bounds__(256) k_pair32(Dev D) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    if (Q && D.st[r].q_done) return;
+    const RepDev &R = D.rep[r];
+    const bool act = threadIdx.x < D.tile_n[t];
+    const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
+    const int4 pi = D.pfix[i];
+    const int ti = pi.w & 1;
+    const float4 dri = Q ? make_float4(0.f, 0.f, 0.f, 0.f) : D.dr32[i];
+    const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
+    const float e0 = R.epsf[ti][0], e1 = R.epsf[ti][1];
+    const float s0 = R.sig2f[ti][0], s1 = R.sig2f[ti][1];
+    const float h0 = R.shiftf[ti][0], h1 = R.shiftf[ti][1];
+    const float rc2 = D.rc2f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+    const int nn = act ? D.nnb[i] : 0;
+    const int *nb = D.nbr + i;
+    for (int k = 0; k < nn; ++k) {
+        const int j = __ldg(nb + (size_t)k * D.natom);
+        const int4 pj = D.pfix[j];
+        const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
+        const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
+        const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < rc2) {
+            const int tj = pj.w & 1;
+            const float eps = tj ? e1 : e0;
+            const float ir2 = __frcp_rn(r2);
+            const float s2 = (tj ? s1 : s0) * ir2;
+            const float s6 = s2 * s2 * s2;
+            const float fr = 24.f * eps * ir2 * s6 * (2.f * s6 - 1.f);
+            fx = fmaf(fr, dx, fx);
+            fy = fmaf(fr, dy, fy);
+            fz = fmaf(fr, dz, fz);
+            e += 0.5f * (4.f * eps * s6 * (s6 - 1.f) - (tj ? h1 : h0));
+            if (!Q) {
+                const float4 drj = D.dr32[j];
+                const float ux = dri.x - drj.x, uy = dri.y - drj.y, uz = dri.z - drj.z;
+                const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+                const float B = 96.f * eps * ir2 * ir2 * s6 * (7.f * s6 - 2.f) * rdu;
+                hx += fmaf(B, dx, -fr * ux);
+                hy += fmaf(B, dy, -fr * uy);
+                hz += fmaf(B, dz, -fr * uz);
+            }
+        }
+    }
+    const int role = act ? ((pi.w >> 8) & 0xff) : -1;
+    if (!Q && role == ROLE_RIGID) {
+        hx += R.kr_nf * dri.x;
+        if (R.dim == 3) hy += R.kr_nf * dri.y;
+    }
+    if (act) {
+        D.f32[i] = make_float4(fx, fy, fz, e);
+        if (!Q) D.h32[i] = make_float4(hx, hy, hz, 0.f);
+    }
+    const bool rig = role == ROLE_RIGID;
+    const bool anyrig = __any_sync(0xffffffffu, rig);
+    if (!Q) {
+        double v[NPART] = {};
+        if (act) {
+            v[PART_D2] = (double)(dri.x * dri.x + dri.y * dri.y + dri.z * dri.z);
+            v[PART_G] = (double)(-(fx * dri.x + fy * dri.y + fz * dri.z));
+            v[PART_V] = (double)e;
+        }
+        if (anyrig && rig) {
+            const dbl4 xi = D.x[i];
+            v[PART_FRIG] = fx; v[PART_FRIG + 1] = fy; v[PART_FRIG + 2] = fz;
+            v[PART_HRIG] = hx; v[PART_HRIG + 1] = hy; v[PART_HRIG + 2] = hz;
+            v[PART_DRRIG] = dri.x; v[PART_DRRIG + 1] = dri.y; v[PART_DRRIG + 2] = dri.z;
+            v[PART_XRIG] = xi.x; v[PART_XRIG + 1] = xi.y; v[PART_XRIG + 2] = xi.z;
+        }
+        cta_reduce<NPART>(v, D.part + (size_t)t * NPART, -1);
+    } else {
+        double v[QPART] = {};
+        if (role == ROLE_MOBILE) {
+            const float4 vv = D.v32[i];
+            v[QP_FMAX2] = (double)fx * fx + (double)fy * fy + (double)fz * fz;
+            v[QP_P] = (double)(fx * vv.x + fy * vv.y + fz * vv.z);
+            v[QP_VV] = (double)(vv.x * vv.x + vv.y * vv.y + vv.z * vv.z);
+            v[QP_FF] = v[QP_FMAX2];
+        }
+        if (rig) {
+            const dbl4 xi = D.x[i];
+            v[QP_FRIG] = fx; v[QP_FRIG + 1] = fy; v[QP_FRIG + 2] = fz;
+            v[QP_XRIG] = xi.x; v[QP_XRIG + 1] = xi.y; v[QP_XRIG + 2] = xi.z;
+        }
+        cta_reduce<QPART>(v, D.part + (size_t)t * NPART, QP_FMAX2);
+    }
+}
+
+// ---------------------------------------------------------------- per-replica scalars
+// Gathers the replica's tile sums (warp q sums slot q over the tiles in a
+// fixed order) and evaluates, in FP64:
+//   x_T = centre of the rigid layer, spring/load gradient gs;
+//   G = grad V . dr (LJ part + gs . sum_rigid dr / n_rig);
+//   d = sqrt(sum dr^2) (Eq. 7), sigma = G / d (Eq. 5), DeltaV_1 (Eq. 14);
+//   bias coefficients: F_tot = F + ca (H dr - F) + cb dr, ca = -DeltaV'/d,
+//   cb = DeltaV' sigma / d^2 (from grad sigma = (H dr + g)/d - sigma dr/d^2);
+//   rigid-body force = sum_rigid F - gs - DeltaV' sum_rigid grad sigma;
+//   body kicks and the clocks: t_h += dt exp(DeltaV / kT) (Eq. 3).
+__device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, double ksum) {
+    const RepDev &R = D.rep[r];
+    RepState &S = D.st[r];
+    Scal &C = D.sc[r];
+    const int nr = R.nrig, dim = R.dim, vert = R.vert;
+    double xT[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
+    if (nr > 0) {
+        for (int a = 0; a < 3; ++a) xT[a] = acc[PART_XRIG + a] / (double)nr;
+        gs[0] = R.kspring * (xT[0] - R.slider[0]);
+        if (dim == 3) gs[1] = R.kspring * (xT[1] - R.slider[1]);
+        gs[vert] = R.fnormal;
+    }
+    double G = acc[PART_G];
+    if (nr > 0) G += (gs[0] * acc[PART_DRRIG] + gs[1] * acc[PART_DRRIG + 1] + gs[2] * acc[PART_DRRIG + 2]) / (double)nr;
+    const double d = sqrt(acc[PART_D2]);
+    const double sig = d > 0.0 ? G / d : 0.0;
+    double dV = 0.0, dVp = 0.0;
+    if (D.bias_on) dv1(R, sig, dV, dVp);
+    const double ca = d > 0.0 ? -dVp / d : 0.0;
+    const double cb = d > 0.0 ? dVp * sig / (d * d) : 0.0;
+    double fb[3] = {0, 0, 0};
+    if (nr > 0)
+        for (int a = 0; a < 3; ++a) {
+            const double grig = -acc[PART_FRIG + a] + gs[a];
+            const double srig = d > 0.0 ? (acc[PART_HRIG + a] + grig) / d - sig * acc[PART_DRRIG + a] / (d * d) : 0.0;
+            fb[a] = acc[PART_FRIG + a] - gs[a] - dVp * srig;
+        }
+    double ext = 0.0;
+    if (nr > 0) {
+        ext = 0.5 * R.kspring * (xT[0] - R.slider[0]) * (xT[0] - R.slider[0]);
+        if (dim == 3) ext += 0.5 * R.kspring * (xT[1] - R.slider[1]) * (xT[1] - R.slider[1]);
+        ext += R.fnormal * xT[vert];
+    }
+    C.d = d; C.sigma = sig; C.dV = dV; C.dVp = dVp; C.G = G;
+    C.Vlj = acc[PART_V];
+    C.V = acc[PART_V] + ext;
+    C.FR = R.kspring * (R.slider[0] - xT[0]);
+    C.ca = ca; C.cb = cb;
+    for (int a = 0; a < 3; ++a) { C.xT[a] = xT[a]; C.fbody[a] = fb[a]; }
+    // clocks and the rigid body
+    const double h = D.dt;
+    double vb[3] = {S.vbody[0], S.vbody[1], S.vbody[2]};
+    if (mode & MODE_CLOSE) {
+        if (nr > 0)
+            for (int a = 0; a < dim; ++a) vb[a] += 0.5 * h * fb[a] / (double)nr;
+        for (int a = 0; a < 3; ++a) S.vbody_full[a] = vb[a];
+    }
+    for (int a = 0; a < 3; ++a) C.vb_mid[a] = vb[a];
+    C.step_cur = S.step;
+    if (mode & MODE_OPEN) {
+        S.t_h += h * exp(dV / R.kT);
+        S.t_md += h;
+        S.step += 1;
+        if (nr > 0)
+            for (int a = 0; a < dim; ++a) vb[a] += 0.5 * h * fb[a] / (double)nr;
+    }
+    for (int a = 0; a < 3; ++a) { C.vb_new[a] = vb[a]; S.vbody[a] = vb[a]; }
+    S.K = ksum + 0.5 * (double)nr * (S.vbody_full[0] * S.vbody_full[0] + S.vbody_full[1] * S.vbody_full[1] +
+                                     S.vbody_full[2] * S.vbody_full[2]);
+    if (D.rebuild[r]) {
+        if (D.rebuild[r] == 1) S.n_rebuild += 1;
+        D.rebuild[r] = 0;
+    }
+}
+
+// blockDim = 32 * (NPART + 1): warp q < NPART sums partial slot q, warp NPART sums K.
+__global__ void k_scalar(Dev D, int mode) {
+    const int r = blockIdx.x;
+    const RepDev &R = D.rep[r];
+    __shared__ double acc[NPART + 1];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int t = R.tile0 + lane; t < R.tile0 + R.ntile; t += 32)
+        a += (w < NPART) ? D.part[(size_t)t * NPART + w] : D.kpart[t];
+    a = warp_sum(a);
+    if (lane == 0) acc[w] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) scalar_eval(D, r, mode, acc, acc[NPART]);
+}
+
+// Kinetic energy of the last full step (observables only).
+__global__ void k_obs(Dev D) {
+    const int r = blockIdx.x;
+    const RepDev &R = D.rep[r];
+    RepState &S = D.st[r];
+    double a = 0.0;
+    for (int t = R.tile0 + (int)threadIdx.x; t < R.tile0 + R.ntile; t += 32) a += D.kpart[t];
+    a = warp_sum(a);
+    if (threadIdx.x == 0)
+        S.K = a + 0.5 * (double)R.nrig * (S.vbody_full[0] * S.vbody_full[0] + S.vbody_full[1] * S.vbody_full[1] +
+                                          S.vbody_full[2] * S.vbody_full[2]);
+}
+
+// ---------------------------------------------------------------- integrator
+// BAOAB (reading: Langevin in place of the paper's Nose-Hoover chain):
+//   CLOSE: v += dt/2 F_tot                      (end of the previous step)
+//   OPEN:  v += dt/2 F_tot; x += dt/2 v; v = c v + s xi; x += dt/2 v
+// Mobile atoms only; rigid atoms follow the body velocity; fixed atoms stay.
+__device__ __forceinline__ void post_move(const Dev &D, const RepDev &R, int r, int i, dbl4 x, int4 p) {
+    const int4 q = fix_pos(R, x, p.w);
+    D.pfix[i] = q;
+    const int4 b = D.pfixb[i];
+    const float ex = (float)(int)((unsigned)q.x - (unsigned)b.x) * R.fx_lsb[0];
+    const float ey = (float)(int)((unsigned)q.y - (unsigned)b.y) * R.fx_lsb[1];
+    const float ez = (float)(int)((unsigned)q.z - (unsigned)b.z) * R.fx_lsb[2];
+    if (ex * ex + ey * ey + ez * ez > D.half_skin2_f) D.rebuild[r] = 1;
+    const double zv = R.vert == 2 ? x.z : x.y;
+    if (!(fabs(zv - R.fx_origin[R.vert]) < R.open_lim) || !isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z))
+        set_err(D, HD_ERR_NUMERIC, i, r);
+}
+
+__global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    const RepDev &R = D.rep[r];
+    const Scal &C = D.sc[r];
+    const bool act = threadIdx.x < D.tile_n[t];
+    const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
+    const int4 p = D.pfix[i];
+    const int role = act ? ((p.w >> 8) & 0xff) : ROLE_FIXED;
+    double kin = 0.0;
+    if (role != ROLE_FIXED) {
+        const double h = D.dt;
+        dbl4 x = D.x[i], v = D.v64[i];
+        if (role == ROLE_MOBILE) {
+            const dbl4 F = D.f64[i], H = D.h64[i], dr = D.dr64[i];
+            const double ca = C.ca, cb = C.cb;
+            const double Fx = F.x + ca * (H.x - F.x) + cb * dr.x;
+            const double Fy = F.y + ca * (H.y - F.y) + cb * dr.y;
+            const double Fz = F.z + ca * (H.z - F.z) + cb * dr.z;
+            const bool three = R.dim == 3;
+            if (mode & MODE_KIN) kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+            if (mode & MODE_CLOSE) {
+                v.x += 0.5 * h * Fx;
+                v.y += 0.5 * h * Fy;
+                if (three) v.z += 0.5 * h * Fz;
+                kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+            }
+            if (mode & MODE_OPEN) {
+                v.x += 0.5 * h * Fx;
+                v.y += 0.5 * h * Fy;
+                if (three) v.z += 0.5 * h * Fz;
+                x.x += 0.5 * h * v.x;
+                x.y += 0.5 * h * v.y;
+                if (three) x.z += 0.5 * h * v.z;
+                double n0, n1, n2, n3;
+                normals64(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 0), n0, n1);
+                v.x = R.c_ou * v.x + R.s_ou * n0;
+                v.y = R.c_ou * v.y + R.s_ou * n1;
+                if (three) {
+                    normals64(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 1), n2, n3);
+                    v.z = R.c_ou * v.z + R.s_ou * n2;
+                }
+                x.x += 0.5 * h * v.x;
+                x.y += 0.5 * h * v.y;
+                if (three) x.z += 0.5 * h * v.z;
+            }
+        } else {
+            if (mode & MODE_CLOSE) v = make_dbl4(C.vb_mid[0], C.vb_mid[1], C.vb_mid[2], 0.0);
+            if (mode & MODE_OPEN) {
+                x.x += 0.5 * h * C.vb_new[0];
+                x.y += 0.5 * h * C.vb_new[1];
+                x.z += 0.5 * h * C.vb_new[2];
+                x.x += 0.5 * h * C.vb_new[0];
+                x.y += 0.5 * h * C.vb_new[1];
+                x.z += 0.5 * h * C.vb_new[2];
+                v = make_dbl4(C.vb_new[0], C.vb_new[1], C.vb_new[2], 0.0);
+            }
+        }
+        D.v64[i] = v;
+        if (mode & MODE_OPEN) {
+            D.x[i] = x;
+            const dbl4 xo = D.xo[i];
+            D.dr64[i] = make_dbl4(x.x - xo.x, x.y - xo.y, x.z - xo.z, 0.0);
+            post_move(D, R, r, i, x, p);
+        }
+    }
+    if (mode & (MODE_CLOSE | MODE_KIN)) {
+        double v1[1] = {kin};
+        cta_reduce<1>(v1, D.kpart + t, -1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    const RepDev &R = D.rep[r];
+    const Scal &C = D.sc[r];
+    const bool act = threadIdx.x < D.tile_n[t];
+    const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
+    const int4 p = D.pfix[i];
+    const int role = act ? ((p.w >> 8) & 0xff) : ROLE_FIXED;
+    float kin = 0.f;
+    if (role != ROLE_FIXED) {
+        const float hh = (float)(0.5 * D.dt);
+        float4 v = D.v32[i];
+        dbl4 x = D.x[i];
+        if (role == ROLE_MOBILE) {
+            const float4 F = D.f32[i], H = D.h32[i], dr = D.dr32[i];
+            const float ca = (float)C.ca, cb = (float)C.cb;
+            const float Fx = fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
+            const float Fy = fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
+            const float Fz = fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
+            const bool three = R.dim == 3;
+            if (mode & MODE_KIN) kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+            if (mode & MODE_CLOSE) {
+                v.x = fmaf(hh, Fx, v.x);
+                v.y = fmaf(hh, Fy, v.y);
+                if (three) v.z = fmaf(hh, Fz, v.z);
+                kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+            }
+            if (mode & MODE_OPEN) {
+                v.x = fmaf(hh, Fx, v.x);
+                v.y = fmaf(hh, Fy, v.y);
+                if (three) v.z = fmaf(hh, Fz, v.z);
+                const float ax = v.x, ay = v.y, az = v.z;
+                float n0, n1, n2, n3;
+                normals32(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 0), n0, n1);
+                v.x = fmaf(R.c_ouf, v.x, R.s_ouf * n0);
+                v.y = fmaf(R.c_ouf, v.y, R.s_ouf * n1);
+                if (three) {
+                    normals32(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 1), n2, n3);
+                    v.z = fmaf(R.c_ouf, v.z, R.s_ouf * n2);
+                }
+                x.x += (double)(hh * (ax + v.x));
+                x.y += (double)(hh * (ay + v.y));
+                if (three) x.z += (double)(hh * (az + v.z));
+            }
+        } else {
+            if (mode & MODE_CLOSE) v = make_float4((float)C.vb_mid[0], (float)C.vb_mid[1], (float)C.vb_mid[2], 0.f);
+            if (mode & MODE_OPEN) {
+                const double h = D.dt;
+                x.x += 0.5 * h * C.vb_new[0];
+                x.y += 0.5 * h * C.vb_new[1];
+                x.z += 0.5 * h * C.vb_new[2];
+                x.x += 0.5 * h * C.vb_new[0];
+                x.y += 0.5 * h * C.vb_new[1];
+                x.z += 0.5 * h * C.vb_new[2];
+                v = make_float4((float)C.vb_new[0], (float)C.vb_new[1], (float)C.vb_new[2], 0.f);
+            }
+        }
+        D.v32[i] = v;
+        if (mode & MODE_OPEN) {
+            D.x[i] = x;
+            const dbl4 xo = D.xo[i];
+            D.dr32[i] = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
+            post_move(D, R, r, i, x, p);
+        }
+    }
+    if (mode & (MODE_CLOSE | MODE_KIN)) {
+        double v1[1] = {(double)kin};
+        cta_reduce<1>(v1, D.kpart + t, -1);
+    }
+}
+
+// ---------------------------------------------------------------- quench
+__global__ void k_qinit(Dev Q, Dev M) {
+    // Q: quench view (x = copy), M: MD view
+    const int t = blockIdx.x, r = Q.tile_rep[t];
+    if (threadIdx.x == 0 && t == Q.rep[r].tile0) {
+        RepState &S = Q.st[r];
+        S.q_dt = Q.q_step;
+        S.q_alpha = 0.1;
+        S.q_npos = 0;
+        S.q_iter = 0;
+        S.q_done = 0;
+        S.q_flag = 0;
+        S.q_fmax = 0.0;
+        S.q_vb[0] = S.q_vb[1] = S.q_vb[2] = 0.0;
+        Q.qdisp[r] = 0ull;
+        Q.rebuild[r] = 2;
+    }
+    if (threadIdx.x >= Q.tile_n[t]) return;
+    const int i = Q.tile_start[t] + threadIdx.x;
+    Q.x[i] = M.x[i];
+    Q.pfix[i] = M.pfix[i];
+    if (Q.prec == HD_FP64) Q.v64[i] = make_dbl4(0, 0, 0, 0);
+    else Q.v32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Convergence test and FIRE bookkeeping (reading of Bitzek et al. 2006: mix
+// with the alpha of this step, then grow/shrink dt and alpha).
+__global__ void k_qscalar(Dev D, int max_iter) {
+    const int r = blockIdx.x;
+    const RepDev &R = D.rep[r];
+    RepState &S = D.st[r];
+    Scal &C = D.sc[r];
+    if (S.q_done) return;
+    __shared__ double acc[QPART];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < QPART) {
+        double a = (w == QP_FMAX2) ? 0.0 : 0.0;
+        for (int t = R.tile0 + lane; t < R.tile0 + R.ntile; t += 32) {
+            const double v = D.part[(size_t)t * NPART + w];
+            a = (w == QP_FMAX2) ? fmax(a, v) : a + v;
+        }
+        a = (w == QP_FMAX2) ? warp_max(a) : warp_sum(a);
+        if (lane == 0) acc[w] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int nr = R.nrig, dim = R.dim;
+    double fb[3] = {0, 0, 0};
+    double fm2 = acc[QP_FMAX2];
+    if (nr > 0) {
+        double xT[3], gs[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) xT[a] = acc[QP_XRIG + a] / (double)nr;
+        gs[0] = R.kspring * (xT[0] - R.slider[0]);
+        if (dim == 3) gs[1] = R.kspring * (xT[1] - R.slider[1]);
+        gs[R.vert] = R.fnormal;
+        for (int a = 0; a < 3; ++a) fb[a] = acc[QP_FRIG + a] - gs[a];
+        fm2 = fmax(fm2, fb[0] * fb[0] + fb[1] * fb[1] + fb[2] * fb[2]);
+    }
+    const double fmax_ = sqrt(fm2);
+    S.q_fmax = fmax_;
+    if (fmax_ < D.q_ftol || S.q_iter >= max_iter) {
+        S.q_done = 1;
+        C.q_active = 0;
+        return;
+    }
+    C.q_active = 1;
+    for (int a = 0; a < 3; ++a) C.q_fbody[a] = fb[a];
+    if (D.q_method == 1) {
+        double pw = acc[QP_P], vv = acc[QP_VV], ff = acc[QP_FF];
+        if (nr > 0)
+            for (int a = 0; a < dim; ++a) {
+                pw += fb[a] * S.q_vb[a];
+                vv += (double)nr * S.q_vb[a] * S.q_vb[a];
+                ff += fb[a] * fb[a] / (double)nr;
+            }
+        double alpha = S.q_alpha, dt = S.q_dt;
+        double vb[3] = {S.q_vb[0], S.q_vb[1], S.q_vb[2]};
+        if (pw > 0.0) {
+            const double mix = ff > 0.0 ? alpha * sqrt(vv) / sqrt(ff) : 0.0;
+            C.q_mix = mix;
+            C.q_zero = 0;
+            if (nr > 0)
+                for (int a = 0; a < dim; ++a) vb[a] = (1.0 - alpha) * vb[a] + mix * fb[a] / (double)nr;
+            S.q_npos += 1;
+            if (S.q_npos > 5) {
+                dt = dt * 1.1 < 10.0 * D.q_step ? dt * 1.1 : 10.0 * D.q_step;
+                alpha *= 0.99;
+            }
+        } else {
+            C.q_mix = 0.0;
+            C.q_zero = 1;
+            vb[0] = vb[1] = vb[2] = 0.0;
+            dt *= 0.5;
+            alpha = 0.1;
+            S.q_npos = 0;
+        }
+        C.q_alpha = S.q_alpha;   // the alpha this step mixes with
+        C.q_dt = dt;             // the dt this step moves with
+        S.q_alpha = alpha;
+        S.q_dt = dt;
+        if (nr > 0)
+            for (int a = 0; a < dim; ++a) vb[a] += dt * fb[a] / (double)nr;
+        for (int a = 0; a < 3; ++a) { S.q_vb[a] = vb[a]; C.q_vb[a] = vb[a]; }
+    }
+    S.q_iter += 1;
+}
+
+// Per-atom quench move.  SD: x += a F (body: a F_body / n_rig).  FIRE: mix,
+// or zero, the velocity, then a semi-implicit Euler step.
+template <typename V4>
+__device__ __forceinline__ void qmove(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
+                                      double fx, double fy, double fz, V4 *vq) {
+    dbl4 x = D.x[i];
+    const int dim = R.dim;
+    if (D.q_method == 0) {
+        const double a = D.q_step;
+        if (role == ROLE_MOBILE) {
+            x.x += a * fx;
+            x.y += a * fy;
+            if (dim == 3) x.z += a * fz;
+        } else {
+            const double inr = 1.0 / (double)R.nrig;
+            x.x += a * C.q_fbody[0] * inr;
+            x.y += a * C.q_fbody[1] * inr;
+            if (dim == 3) x.z += a * C.q_fbody[2] * inr;
+        }
+    } else {
+        const double dt = C.q_dt;
+        if (role == ROLE_MOBILE) {
+            V4 v = vq[i];
+            double vx = v.x, vy = v.y, vz = v.z;
+            if (C.q_zero) {
+                vx = vy = vz = 0.0;
+            } else {
+                vx = (1.0 - C.q_alpha) * vx + C.q_mix * fx;
+                vy = (1.0 - C.q_alpha) * vy + C.q_mix * fy;
+                vz = (1.0 - C.q_alpha) * vz + C.q_mix * fz;
+            }
+            vx += dt * fx;
+            vy += dt * fy;
+            if (dim == 3) vz += dt * fz;
+            else vz = 0.0;
+            x.x += dt * vx;
+            x.y += dt * vy;
+            if (dim == 3) x.z += dt * vz;
+            v.x = vx; v.y = vy; v.z = vz;
+            vq[i] = v;
+        } else {
+            x.x += dt * C.q_vb[0];
+            x.y += dt * C.q_vb[1];
+            if (dim == 3) x.z += dt * C.q_vb[2];
+        }
+    }
+    D.x[i] = x;
+    post_move(D, R, r, i, x, p);
+}
+
+__global__ void __launch_bounds__(256) k_qupdate(Dev D) {
+    const int t = blockIdx.x, r = D.tile_rep[t];
+    const Scal &C = D.sc[r];
+    if (!C.q_active || D.st[r].q_done) return;
+    if (threadIdx.x >= D.tile_n[t]) return;
+    const int i = D.tile_start[t] + threadIdx.x;
+    const RepDev &R = D.rep[r];
+    const int4 p = D.pfix[i];
+    const int role = (p.w >> 8) & 0xff;
+    if (role == ROLE_FIXED) return;
+    if (D.prec == HD_FP64) {
+        const dbl4 f = D.f64[i];
+        qmove(D, R, C, r, i, p, role, f.x, f.y, f.z, D.v64);
+    } else {
+        const float4 f = D.f32[i];
+        qmove(D, R, C, r, i, p, role, (double)f.x, (double)f.y, (double)f.z, D.v32);
+    }
+}
+
+// Largest displacement of the quenched copy from r_O per replica (minimum
+// image, FP64, the oracle's operation order); stored as the bits of the
+// non-negative double so that an integer max is the FP64 max.
+__global__ void k_qdisp(Dev Q) {
+    const int t = blockIdx.x, r = Q.tile_rep[t];
+    if (threadIdx.x >= Q.tile_n[t]) return;
+    const int i = Q.tile_start[t] + threadIdx.x;
+    const RepDev &R = Q.rep[r];
+    const dbl4 a = Q.x[i], b = Q.xo[i];
+    double d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z;
+    if (R.periodic[0]) d0 = __dsub_rn(d0, __dmul_rn(R.L[0], rint(__ddiv_rn(d0, R.L[0]))));
+    if (R.periodic[1]) d1 = __dsub_rn(d1, __dmul_rn(R.L[1], rint(__ddiv_rn(d1, R.L[1]))));
+    if (R.periodic[2]) d2 = __dsub_rn(d2, __dmul_rn(R.L[2], rint(__ddiv_rn(d2, R.L[2]))));
+    const double m = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+    atomicMax(Q.qdisp + r, (unsigned long long)__double_as_longlong(m));
+}
+
+// r_O <- quenched copy for replicas with adopt[r] != 0; refresh r - r_O.
+__global__ void k_adopt(Dev Q, Dev M, const int *adopt) {
+    const int t = blockIdx.x, r = M.tile_rep[t];
+    if (!adopt[r] || threadIdx.x >= M.tile_n[t]) return;
+    const int i = M.tile_start[t] + threadIdx.x;
+    const dbl4 q = Q.x[i];
+    M.xo[i] = make_dbl4(q.x, q.y, q.z, 0.0);
+    const dbl4 x = M.x[i];
+    if (M.prec == HD_FP64) M.dr64[i] = make_dbl4(x.x - q.x, x.y - q.y, x.z - q.z, 0.0);
+    else M.dr32[i] = make_float4((float)(x.x - q.x), (float)(x.y - q.y), (float)(x.z - q.z), 0.f);
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int nthr(const Dev &D) { return D.block; }
+
+void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s) {
+    k_init<<<D.ntile, nthr(D), 0, s>>>(D, draw_vel);
+}
+void launch_rebuild(const Dev &D, cudaStream_t s) {
+    k_cell_clear<<<D.nrep, 256, 0, s>>>(D);
+    k_bin<<<D.ntile, nthr(D), 0, s>>>(D);
+    k_nlist<<<D.ntile, nthr(D), 0, s>>>(D);
+}
+void launch_pair(const Dev &D, bool quench, cudaStream_t s) {
+    if (D.prec == HD_FP64) {
+        if (quench) k_pair64<true><<<D.ntile, nthr(D), 0, s>>>(D);
+        else k_pair64<false><<<D.ntile, nthr(D), 0, s>>>(D);
+    } else {
+        if (quench) k_pair32<true><<<D.ntile, nthr(D), 0, s>>>(D);
+        else k_pair32<false><<<D.ntile, nthr(D), 0, s>>>(D);
+    }
+}
+void launch_scalar(const Dev &D, int mode, cudaStream_t s) {
+    k_scalar<<<D.nrep, 32 * (NPART + 1), 0, s>>>(D, mode);
+}
+void launch_update(const Dev &D, int mode, cudaStream_t s) {
+    if (D.prec == HD_FP64) k_update64<<<D.ntile, nthr(D), 0, s>>>(D, mode);
+    else k_update32<<<D.ntile, nthr(D), 0, s>>>(D, mode);
+}
+void launch_obs(const Dev &D, cudaStream_t s) { k_obs<<<D.nrep, 32, 0, s>>>(D); }
+void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s) { k_qinit<<<Q.ntile, nthr(Q), 0, s>>>(Q, M); }
+void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s) {
+    launch_rebuild(Q, s);
+    launch_pair(Q, true, s);
+    k_qscalar<<<Q.nrep, 32 * QPART, 0, s>>>(Q, max_iter);
+    k_qupdate<<<Q.ntile, nthr(Q), 0, s>>>(Q);
+}
+void launch_qdisp(const Dev &Q, cudaStream_t s) { k_qdisp<<<Q.ntile, nthr(Q), 0, s>>>(Q); }
+void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s) {
+    k_adopt<<<M.ntile, nthr(M), 0, s>>>(Q, M, adopt);
+}
+
+}  // namespace hd

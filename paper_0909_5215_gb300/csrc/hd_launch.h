@@ -1,0 +1,21 @@
+// hd_launch.h -- host-side launchers of the kernels in hd_kernels.cu and
+// hd_persist.cu.  Every launcher queues work on stream s and returns at once.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hd_internal.cuh"
+
+namespace hd {
+
+void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s);
+void launch_rebuild(const Dev &D, cudaStream_t s);            // 3 kernels, flag-gated per replica
+void launch_pair(const Dev &D, bool quench, cudaStream_t s);
+void launch_scalar(const Dev &D, int mode, cudaStream_t s);
+void launch_update(const Dev &D, int mode, cudaStream_t s);
+void launch_obs(const Dev &D, cudaStream_t s);
+void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s);
+void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 6 kernels
+void launch_qdisp(const Dev &Q, cudaStream_t s);
+void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s);
+
+}  // namespace hd

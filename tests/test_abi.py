@@ -1,0 +1,133 @@
+"""The C-ABI library builds, loads and exports what include/hd.h declares.
+
+No GPU: only host-side logic is exercised (workspace sizing, argument
+checks that return before any CUDA call) plus the binding's struct layout,
+checked against the C compiler's view of include/hd.h.
+"""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, small2d, small3d
+
+HDR = os.path.join(ROOT, "include", "hd.h")
+
+
+@pytest.fixture(scope="module")
+def hdlib():
+    from paper_0909_5215_gb300 import _build, hd
+    _build.build()
+    return hd
+
+
+def declared_functions():
+    text = open(HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hd_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("hd_create", "hd_set_slider", "hd_step", "hd_quench", "hd_read"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(hdlib):
+    out = subprocess.run(["nm", "-D", "--defined-only", hdlib._build.OUT], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (hd_[a-z_]+)\b", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    L = hdlib.lib()
+    for n in declared_functions():
+        assert hasattr(L, n)
+    assert set(hdlib.SYMBOLS) <= set(declared_functions())
+
+
+def test_struct_layout_matches_header(hdlib, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "hd.h"
+#define F(T, m) printf("%s.%s %zu\n", #T, #m, offsetof(T, m))
+int main(void) {
+  printf("sizeof.hd_replica_desc %zu\nsizeof.hd_params %zu\n", sizeof(hd_replica_desc), sizeof(hd_params));
+  F(hd_replica_desc, pos); F(hd_replica_desc, role); F(hd_replica_desc, box); F(hd_replica_desc, periodic);
+  F(hd_replica_desc, kT); F(hd_replica_desc, slider); F(hd_replica_desc, dvmax); F(hd_replica_desc, eps);
+  F(hd_replica_desc, sig); F(hd_replica_desc, t_h0); F(hd_replica_desc, step0);
+  F(hd_params, dt); F(hd_params, seed); F(hd_params, maxnb); F(hd_params, cell_cap);
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HDR), "-o", str(exe), str(src)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    import ctypes as C
+    D, P = hdlib.hd_replica_desc, hdlib.hd_params
+    assert int(got["sizeof.hd_replica_desc"]) == C.sizeof(D)
+    assert int(got["sizeof.hd_params"]) == C.sizeof(P)
+    for key, val in got.items():
+        kind, field = key.split(".")
+        if kind == "sizeof":
+            continue
+        cls = D if kind == "hd_replica_desc" else P
+        assert getattr(cls, field).offset == int(val), key
+
+
+def test_workspace_sizing_host_only(hdlib):
+    from paper_0909_5215_gb300 import model as M
+    reps = [small2d(), small3d()]
+    p = M.Params(prec=1)
+    nb = hdlib.workspace_bytes(reps, p)
+    n = sum(r.n for r in reps)
+    assert nb > n * (3 * 32 + 112 * 4) and nb % 256 == 0
+    # FP64 form holds wider velocity/force arrays
+    assert hdlib.workspace_bytes(reps, M.Params(prec=0)) > nb
+    # invalid batches size to 0
+    bad = small2d()
+    bad.role = bad.role.copy()
+    bad.role[0] = 7
+    assert hdlib.workspace_bytes([bad], p) == 0
+    bad = small3d()
+    bad.periodic = np.array([1, 1, 1], dtype=np.uint8)
+    assert hdlib.workspace_bytes([bad], p) == 0
+    assert hdlib.workspace_bytes([small2d()], M.Params(dt=-1.0)) == 0
+    assert hdlib.workspace_bytes([small2d()], p, block=100) == 0
+    assert hdlib.workspace_bytes([small2d()], p, maxnb=1000) == 0
+
+
+def test_create_rejects_bad_arguments_before_any_device_work(hdlib):
+    import ctypes as C
+    from paper_0909_5215_gb300 import model as M
+    reps = [small2d()]
+    descs, keep = hdlib.make_descs(reps)
+    prm = hdlib.make_params(M.Params(prec=1))
+    ctx = C.c_void_p()
+    # NULL workspace
+    st = hdlib.hd_create(descs, 1, prm, 0, 1 << 20, 0, ctx)
+    assert st == hdlib.HD_ERR_ARG and "workspace" in hdlib.hd_last_error(ctx)
+    hdlib.hd_destroy(ctx)
+    # too small a workspace (a fake, never dereferenced, aligned address)
+    ctx = C.c_void_p()
+    st = hdlib.hd_create(descs, 1, prm, 1 << 20, 256, 0, ctx)
+    assert st == hdlib.HD_ERR_NOMEM
+    hdlib.hd_destroy(ctx)
+    # misaligned workspace
+    ctx = C.c_void_p()
+    st = hdlib.hd_create(descs, 1, prm, (1 << 20) + 8, 1 << 30, 0, ctx)
+    assert st == hdlib.HD_ERR_ARG
+    hdlib.hd_destroy(ctx)
+    del keep
+
+
+def test_binding_fails_loudly_without_library(hdlib, monkeypatch):
+    from paper_0909_5215_gb300 import _build
+    monkeypatch.setattr(_build, "OUT", "/nonexistent/libhdslide.so")
+    monkeypatch.setattr(hdlib, "_lib", None)
+    with pytest.raises(RuntimeError):
+        hdlib.lib()

