@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--workload", default="afm3d_hyper64")
     ap.add_argument("--prec", default="split", choices=["split", "fp64"])
     ap.add_argument("--md-steps", type=int, default=500)
-    ap.add_argument("--quench-iters", type=int, default=500)
+    ap.add_argument("--quench-iters", type=int, default=300)
     ap.add_argument("--quench-ftol", type=float, default=1e-3)
     ap.add_argument("--driver", default="auto", choices=["auto", "kernels", "persistent"])
     ap.add_argument("--block", type=int, default=0)
@@ -239,7 +239,8 @@ def run_ours(args):
     info0 = b.info()
     b.timing(2)
     b.timing(1)
-    th0 = b.obs()[:, 2].copy()
+    ob0 = b.obs()
+    th0 = ob0[:, 2].copy()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -266,7 +267,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     tim = b.timing(0)
     info1 = b.info()
-    th1 = b.obs()[:, 2]
+    ob1 = b.obs()
+    th1 = ob1[:, 2]
     sec = ms / 1000.0
     if world > 1:
         import torch.distributed as dist
@@ -363,6 +365,9 @@ def run_ours(args):
             "hypertime_per_s": dth / sec,
             "md_only": {"value": atom_steps / (md_ms / 1000.0), "unit": UNIT},
             "roofline": roof, "phases_ms": phases, "fp64_form": fp64,
+            "list_rebuilds_per_replica_step": float((ob1[:, 12] - ob0[:, 12]).sum()) / (len(reps) * args.md_steps *
+                                                                                          args.steps),
+            "quench_iters_mean": float(ob1[:, 14].mean()),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

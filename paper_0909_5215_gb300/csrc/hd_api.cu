@@ -25,12 +25,16 @@ struct Plan {
     int nrep = 0, natom = 0, ntile = 0, maxnb = 0, cell_cap = 0, ncell = 0, block = 128, prec = 0;
     std::vector<RepDev> rep;
     std::vector<int> tile_rep, tile_start, tile_n;
+    // storage order: atoms of a replica are held cell-major (cells of the
+    // initial configuration, z then y then x, input order inside a cell);
+    // slot_orig[global slot] = the atom's index in the replica's input arrays
+    std::vector<int> slot_orig;
     size_t bytes = 0;
     // offsets
     size_t o_rep, o_st, o_sc, o_trep, o_tstart, o_tn, o_part, o_qpart, o_kpart;
     size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
-    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt;
+    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig;
 };
 
 size_t take(size_t &cur, size_t bytes) {
@@ -115,8 +119,25 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                     mn = std::min(mn, d.pos[3 * i + a]);
                     mx = std::max(mx, d.pos[3 * i + a]);
                 }
-                double span = 64.0;
-                while (span < 4.0 * (mx - mn) + 64.0) span *= 2.0;
+                // Common fixed-point unit: when every periodic axis has the same
+                // length L, the open axis uses L 2^k / 2^32 per unit, so squared
+                // distances are exact integer sums in units of (L / 2^32)^2.
+                const double need = 2.0 * (mx - mn) + 24.0;
+                bool same = true;
+                for (int q = 0; q < d.dim - 1; ++q) same &= d.box[q] == d.box[0];
+                double span;
+                if (same) {
+                    int k = 0;
+                    span = d.box[0];
+                    while (span < need) { span *= 2.0; ++k; }
+                    R.exact_r2 = 1;
+                    R.zshift = k;
+                    R.lsb2_hi = (float)((d.box[0] / 4294967296.0) * (d.box[0] / 4294967296.0));
+                    R.lsb2_lo = (float)((d.box[0] / 4294967296.0) * (d.box[0] / 4294967296.0) - (double)R.lsb2_hi);
+                } else {
+                    span = 64.0;
+                    while (span < need) span *= 2.0;
+                }
                 R.fx_origin[a] = 0.5 * (mn + mx);
                 R.fx_scale[a] = 4294967296.0 / span;
                 R.fx_lsb[a] = (float)(span / 4294967296.0);
@@ -130,11 +151,15 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
             }
             if (R.nc[a] >= 1024) { why = "replica " + std::to_string(r) + ": more than 1023 cells along an axis"; return false; }
         }
+        for (int a = 0; a < 3; ++a) {
+            const double u = R.fx_scale[a] != 0.0 ? 1.0 / R.fx_scale[a] : 0.0;
+            R.lsb_rel[a] = R.fx_lsb[a] != 0.f ? (float)((u - (double)R.fx_lsb[a]) / (double)R.fx_lsb[a]) : 0.f;
+        }
         R.ncell = R.nc[0] * R.nc[1] * R.nc[2];
         R.cell0 = (int)ncell;
-        // occupancy estimate of the initial configuration
+        // occupancy estimate of the initial configuration and the storage order
         {
-            std::vector<int> occ(R.ncell, 0);
+            std::vector<int> occ(R.ncell, 0), key(d.n_atoms);
             for (int i = 0; i < d.n_atoms; ++i) {
                 int c[3];
                 for (int a = 0; a < 3; ++a) {
@@ -145,8 +170,13 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                     else t = (x - (R.fx_origin[a] + R.cell_lo_fix / R.fx_scale[a])) / (rl * (1.0 + 1e-4));
                     c[a] = std::min(R.nc[a] - 1, std::max(0, (int)std::floor(t)));
                 }
-                max_occ = std::max(max_occ, ++occ[(c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0]]);
+                key[i] = (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+                max_occ = std::max(max_occ, ++occ[key[i]]);
             }
+            std::vector<int> order(d.n_atoms);
+            for (int i = 0; i < d.n_atoms; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+            P.slot_orig.insert(P.slot_orig.end(), order.begin(), order.end());
         }
         // interaction constants (Eq. 9 with the shift at rc)
         R.kT = d.kT;
@@ -172,6 +202,9 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                 R.epsf[a][b] = (float)eps;
                 R.sig2f[a][b] = (float)(sig * sig);
                 R.shiftf[a][b] = (float)R.shift[a][b];
+                const double r0sq = std::cbrt(2.0) * sig * sig;   // LJ minimum 2^(1/6) sigma, squared
+                R.r0sq_hi[a][b] = (float)r0sq;
+                R.r0sq_lo[a][b] = (float)(r0sq - (double)R.r0sq_hi[a][b]);
             }
         R.kr_n = nrig > 0 ? d.k_spring / nrig : 0.0;
         R.kr_nf = (float)R.kr_n;
@@ -212,9 +245,9 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_fq = take(cur, N * v4);
     P.o_h = take(cur, N * v4);
     P.o_dr = take(cur, N * v4);
-    P.o_pfix = take(cur, N * 16);
+    P.o_pfix = take(cur, N * sizeof(AtomRec));
     P.o_pfixb = take(cur, N * 16);
-    P.o_qpfix = take(cur, N * 16);
+    P.o_qpfix = take(cur, N * sizeof(AtomRec));
     P.o_qpfixb = take(cur, N * 16);
     P.o_cellid = take(cur, N * 4);
     P.o_nnb = take(cur, N * 4);
@@ -228,6 +261,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_qdisp = take(cur, R * 8);
     P.o_drawvel = take(cur, R * 4);
     P.o_adopt = take(cur, R * 4);
+    P.o_orig = take(cur, N * 4);
     P.bytes = (cur + ALIGN - 1) / ALIGN * ALIGN;
     return true;
 }
@@ -245,6 +279,7 @@ struct hd_ctx {
     int persistent_ctas = 0;
     long long launches = 0;
     std::map<int, cudaGraphExec_t> graphs;
+    std::map<std::string, cudaGraphExec_t> qgraphs;
     std::vector<double> qdisp;
     std::vector<int> qflag;
     long long h2d = 0, d2h = 0;
@@ -303,17 +338,24 @@ struct Timed {
     std::vector<hd_ctx::Span> *sink;
     hd_ctx::Span sp;
     bool on;
+    bool capturing = false;
     Timed(hd_ctx *c_, std::vector<hd_ctx::Span> *sink_, int cat) : c(c_), sink(sink_), on(c_->timing && sink_) {
         if (on) {
             sp.a = get_event(c);
             sp.b = get_event(c);
             sp.cat = cat;
-            cudaEventRecord(sp.a, c->s);
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(c->s, &cs);
+            capturing = cs == cudaStreamCaptureStatusActive;
+            // inside a capture only an external record becomes an event node
+            if (capturing) cudaEventRecordWithFlags(sp.a, c->s, cudaEventRecordExternal);
+            else cudaEventRecord(sp.a, c->s);
         }
     }
     ~Timed() {
         if (on) {
-            cudaEventRecord(sp.b, c->s);
+            if (capturing) cudaEventRecordWithFlags(sp.b, c->s, cudaEventRecordExternal);
+            else cudaEventRecord(sp.b, c->s);
             sink->push_back(sp);
         }
     }
@@ -325,6 +367,8 @@ void harvest(hd_ctx *c, std::vector<hd_ctx::Span> &v, bool recycle) {
         if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
             c->tsum[sp.cat] += ms;
             c->tcnt[sp.cat] += 1;
+        } else {
+            (void)cudaGetLastError();  // an unrecorded span is skipped, not reported later
         }
         if (recycle) {
             c->free_events.push_back(sp.a);
@@ -351,6 +395,8 @@ void fill_dev(hd_ctx *c) {
     D.maxnb = P.maxnb;
     D.cell_cap = P.cell_cap;
     D.ncell = P.ncell;
+    D.max_cells = 0;
+    for (const RepDev &R : P.rep) D.max_cells = std::max(D.max_cells, R.ncell);
     D.prec = P.prec;
     D.block = P.block;
     D.rep = at<RepDev>(b, P.o_rep);
@@ -372,9 +418,8 @@ void fill_dev(hd_ctx *c) {
         D.v32 = at<float4>(b, P.o_v);
         D.f32 = at<float4>(b, P.o_f);
         D.h32 = at<float4>(b, P.o_h);
-        D.dr32 = at<float4>(b, P.o_dr);
     }
-    D.pfix = at<int4>(b, P.o_pfix);
+    D.rec = at<AtomRec>(b, P.o_pfix);
     D.pfixb = at<int4>(b, P.o_pfixb);
     D.cellid = at<int>(b, P.o_cellid);
     D.nnb = at<int>(b, P.o_nnb);
@@ -385,6 +430,7 @@ void fill_dev(hd_ctx *c) {
     D.err = at<int>(b, P.o_err);
     D.bar = at<unsigned int>(b, P.o_bar);
     D.qdisp = at<unsigned long long>(b, P.o_qdisp);
+    D.orig = at<int>(b, P.o_orig);
     // quench view: the copy of the positions and its own velocity, force,
     // fixed-point image, rebuild flags and tile sums
     Dev &Q = c->Q;
@@ -397,7 +443,7 @@ void fill_dev(hd_ctx *c) {
         Q.v32 = at<float4>(b, P.o_vq);
         Q.f32 = at<float4>(b, P.o_fq);
     }
-    Q.pfix = at<int4>(b, P.o_qpfix);
+    Q.rec = at<AtomRec>(b, P.o_qpfix);
     Q.pfixb = at<int4>(b, P.o_qpfixb);
     Q.rebuild = at<int>(b, P.o_qrebuild);
     Q.part = at<double>(b, P.o_qpart);
@@ -446,7 +492,7 @@ void queue_step(hd_ctx *c, int mode, std::vector<hd_ctx::Span> *sink) {
     { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, c->s); }
     { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, mode, c->s); }
     { Timed t(c, sink, T_UPDATE); launch_update(c->D, mode, c->s); }
-    c->launches += 6;
+    c->launches += 7;
 }
 
 void queue_steps(hd_ctx *c, int n, std::vector<hd_ctx::Span> *sink) {
@@ -463,7 +509,7 @@ hd_status refresh_md(hd_ctx *c, bool relist) {
         CK(cudaMemcpyAsync(c->D.rebuild, two.data(), two.size() * 4, cudaMemcpyHostToDevice, c->s));
         c->h2d += (long long)two.size() * 4;
         launch_rebuild(c->D, c->s);
-        c->launches += 3;
+        c->launches += 4;
         CK(cudaStreamSynchronize(c->s));
     }
     launch_pair(c->D, false, c->s);
@@ -507,7 +553,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     CK(cudaMemsetAsync(c->ws, 0, P.bytes, c->s));
     // host staging
     std::vector<dbl4> hx(N), hxo(N);
-    std::vector<int4> hp(N);
+    std::vector<AtomRec> hp(N);
     std::vector<char> hv(N * (P.prec == HD_FP64 ? sizeof(dbl4) : sizeof(float4)));
     std::vector<RepState> hst(P.nrep);
     std::vector<int> draw(P.nrep), two(P.nrep, 2);
@@ -519,24 +565,26 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
         hst[r].t_h = d.t_h0;
         hst[r].t_md = d.t_md0;
         hst[r].step = d.step0;
-        for (int i = 0; i < d.n_atoms; ++i) {
+        if (d.vel)
+            for (int i = 0; i < d.n_atoms; ++i)
+                if (d.role[i] == 2) {  // the body starts with the first rigid atom's velocity
+                    for (int a = 0; a < d.dim; ++a) hst[r].vbody[a] = hst[r].vbody_full[a] = d.vel[3 * i + a];
+                    break;
+                }
+        for (int sl = 0; sl < d.n_atoms; ++sl) {
+            const int i = P.slot_orig[a0 + sl];
             const double *x = d.pos + 3 * i;
             const double *xo = d.pos_ref ? d.pos_ref + 3 * i : x;
-            hx[a0 + i] = make_dbl4(x[0], x[1], x[2], (double)d.type[i]);
-            hxo[a0 + i] = make_dbl4(xo[0], xo[1], xo[2], 0.0);
-            hp[a0 + i] = make_int4(0, 0, 0, (int)d.type[i] | ((int)d.role[i] << 8));
+            hx[a0 + sl] = make_dbl4(x[0], x[1], x[2], (double)d.type[i]);
+            hxo[a0 + sl] = make_dbl4(xo[0], xo[1], xo[2], 0.0);
+            hp[a0 + sl].p = make_int4(0, 0, 0, (int)d.type[i] | ((int)d.role[i] << 8));
+            hp[a0 + sl].d = make_float4(0.f, 0.f, 0.f, 0.f);
             double v[3] = {0, 0, 0};
             if (d.vel && d.role[i] != 0)
                 for (int a = 0; a < 3; ++a) v[a] = d.vel[3 * i + a];
             if (d.dim == 2) v[2] = 0.0;
-            if (d.vel && d.role[i] == 2) {
-                bool first = true;
-                for (int k = 0; k < i; ++k) first &= d.role[k] != 2;
-                if (first)
-                    for (int a = 0; a < 3; ++a) hst[r].vbody[a] = hst[r].vbody_full[a] = v[a];
-            }
-            if (P.prec == HD_FP64) reinterpret_cast<dbl4 *>(hv.data())[a0 + i] = make_dbl4(v[0], v[1], v[2], 0.0);
-            else reinterpret_cast<float4 *>(hv.data())[a0 + i] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+            if (P.prec == HD_FP64) reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
+            else reinterpret_cast<float4 *>(hv.data())[a0 + sl] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
         }
     }
     if (upload_reps(c) != HD_OK) return c->status;
@@ -546,7 +594,8 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     CK(cudaMemcpyAsync((void *)c->D.tile_n, P.tile_n.data(), P.ntile * 4, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->D.x, hx.data(), N * sizeof(dbl4), cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->D.xo, hxo.data(), N * sizeof(dbl4), cudaMemcpyHostToDevice, c->s));
-    CK(cudaMemcpyAsync(c->D.pfix, hp.data(), N * 16, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->D.rec, hp.data(), N * sizeof(AtomRec), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync((void *)c->D.orig, P.slot_orig.data(), N * 4, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->ws + P.o_v, hv.data(), hv.size(), cudaMemcpyHostToDevice, c->s));
     int *d_draw = at<int>(c->ws, P.o_drawvel);
     CK(cudaMemcpyAsync(d_draw, draw.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s));
@@ -557,7 +606,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     launch_scalar(c->D, 0, c->s);
     launch_update(c->D, MODE_KIN, c->s);  // kinetic energy of the initial velocities
     launch_obs(c->D, c->s);
-    c->launches += 8;
+    c->launches += 9;
     CK(cudaGetLastError());
     c->qdisp.assign(P.nrep, 0.0);
     c->qflag.assign(P.nrep, 0);
@@ -644,7 +693,7 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     }
     CK(cudaGraphLaunch(it->second, c->s));
     if (c->timing) c->graph_pending.push_back(key);
-    c->launches += 2 + 6LL * n_steps;
+    c->launches += 2 + 7LL * n_steps;
     return HD_OK;
 }
 
@@ -664,9 +713,35 @@ hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double ste
     c->launches += 1;
     std::vector<RepState> st(R);
     const int chunk = 32;
+    // one CUDA graph per quench setting replays `chunk` iterations
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(c->s, &cs));
+    cudaGraphExec_t qg = nullptr;
+    if (c->s != nullptr && cs == cudaStreamCaptureStatusNone) {
+        char key[128];
+        snprintf(key, sizeof key, "%d/%.17g/%.17g/%d", method, ftol, step_size, max_iter);
+        auto it = c->qgraphs.find(key);
+        if (it == c->qgraphs.end()) {
+            if (c->qgraphs.size() >= 8) {
+                for (auto &g : c->qgraphs) cudaGraphExecDestroy(g.second);
+                c->qgraphs.clear();
+            }
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < chunk; ++k) launch_qiter(Q, max_iter, c->s);
+            CK(cudaStreamEndCapture(c->s, &g));
+            cudaGraphExec_t ge;
+            CK(cudaGraphInstantiate(&ge, g, 0));
+            cudaGraphDestroy(g);
+            it = c->qgraphs.emplace(key, ge).first;
+        }
+        qg = it->second;
+    }
     for (int done_iters = 0; done_iters <= max_iter;) {
-        for (int k = 0; k < chunk; ++k) launch_qiter(Q, max_iter, c->s);
-        c->launches += 6LL * chunk;
+        if (qg) CK(cudaGraphLaunch(qg, c->s));
+        else
+            for (int k = 0; k < chunk; ++k) launch_qiter(Q, max_iter, c->s);
+        c->launches += 7LL * chunk;
         done_iters += chunk;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(st.data(), c->D.st, R * sizeof(RepState), cudaMemcpyDeviceToHost, c->s));
@@ -734,13 +809,14 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         CK(cudaMemcpy(buf.data(), (const char *)dptr + a0 * es, n * es, cudaMemcpyDeviceToHost));
         c->d2h += (long long)(n * es);
         double *o = (double *)h_dst;
-        for (size_t i = 0; i < n; ++i) {
+        for (size_t sl = 0; sl < n; ++sl) {
+            const size_t i = (size_t)P.slot_orig[a0 + sl], si = sl;
             double q[4];
             if (fp64) {
-                const dbl4 v = reinterpret_cast<const dbl4 *>(buf.data())[i];
+                const dbl4 v = reinterpret_cast<const dbl4 *>(buf.data())[si];
                 q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
             } else {
-                const float4 v = reinterpret_cast<const float4 *>(buf.data())[i];
+                const float4 v = reinterpret_cast<const float4 *>(buf.data())[si];
                 q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
             }
             if (comp_w == 3) o[i] = q[3];
@@ -772,24 +848,32 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         if (!need(n * 24)) break;
         return vec3(c->ws + P.o_h, f64, -1);
     case HD_FIELD_NBR_COUNT:
+    case HD_FIELD_CELL: {
         if (!need(n * 4)) break;
-        CK(cudaMemcpy(h_dst, c->D.nnb + a0, n * 4, cudaMemcpyDeviceToHost));
+        std::vector<int> tmp(n);
+        CK(cudaMemcpy(tmp.data(), (field == HD_FIELD_CELL ? c->D.cellid : c->D.nnb) + a0, n * 4,
+                      cudaMemcpyDeviceToHost));
         c->d2h += 4LL * n;
+        int *o = (int *)h_dst;
+        for (size_t sl = 0; sl < n; ++sl) o[P.slot_orig[a0 + sl]] = tmp[sl];
         return HD_OK;
-    case HD_FIELD_CELL:
-        if (!need(n * 4)) break;
-        CK(cudaMemcpy(h_dst, c->D.cellid + a0, n * 4, cudaMemcpyDeviceToHost));
-        c->d2h += 4LL * n;
-        return HD_OK;
+    }
     case HD_FIELD_NBR: {
+        // rows in input numbering, ascending in j
         if (!need(n * P.maxnb * 4)) break;
         std::vector<int> cnt(n), slab(n * P.maxnb);
         CK(cudaMemcpy(cnt.data(), c->D.nnb + a0, n * 4, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy2D(slab.data(), n * 4, c->D.nbr + a0, (size_t)P.natom * 4, n * 4, P.maxnb, cudaMemcpyDeviceToHost));
         c->d2h += 4LL * n * (1 + P.maxnb);
         int *o = (int *)h_dst;
-        for (size_t i = 0; i < n; ++i)
-            for (int k = 0; k < P.maxnb; ++k) o[i * P.maxnb + k] = k < cnt[i] ? slab[(size_t)k * n + i] - (int)a0 : -1;
+        std::vector<int> row;
+        for (size_t sl = 0; sl < n; ++sl) {
+            const int i = P.slot_orig[a0 + sl];
+            row.clear();
+            for (int k = 0; k < cnt[sl] && k < P.maxnb; ++k) row.push_back(P.slot_orig[slab[(size_t)k * n + sl]]);
+            std::sort(row.begin(), row.end());
+            for (int k = 0; k < P.maxnb; ++k) o[(size_t)i * P.maxnb + k] = k < (int)row.size() ? row[k] : -1;
+        }
         return HD_OK;
     }
     case HD_FIELD_OBS: {
@@ -875,6 +959,7 @@ void hd_destroy(hd_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->s);
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    for (auto &g : c->qgraphs) cudaGraphExecDestroy(g.second);
     for (auto &sp : c->pending) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (auto &kv : c->graph_spans)
         for (auto &sp : kv.second) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }

@@ -1,14 +1,17 @@
 // hd_internal.cuh -- device-side data layout and helpers of libhdslide.
 //
 // Layout in HBM (one caller-owned workspace, 256-byte aligned blocks):
-//   per atom, all replicas back to back (atom g of replica r at atom0[r] + local):
+//   per atom, all replicas back to back; inside a replica atoms are held in
+//   cell-major order of the initial configuration (orig[] maps a slot to the
+//   atom's input index, which is also its Philox counter word):
 //     x      dbl4  FP64 position, w = LJ type           (never wrapped)
 //     xo     dbl4  basin minimum r_O
 //     v      dbl4 (FP64 form) | float4 (split form)    velocity
 //     f      dbl4 | float4   LJ force, w = per-atom energy (half of each pair)
 //     h      dbl4 | float4   H.(r - r_O), spring term included
 //     dr     dbl4 | float4   r - r_O
-//     pfix   int4     32-bit fixed-point position, w = type | role << 8
+//     rec    AtomRec  32-bit fixed-point position (w = type | role << 8) and
+//                     FP32 r - r_O of the split form, 32 bytes
 //     pfixb  int4     pfix at the last list build (displacement check)
 //     nbr    int32 [maxnb][natom] column-major Verlet list (global j), nnb int32
 //   per cell: count int32, atoms int32 [cell_cap]
@@ -46,6 +49,13 @@ enum { QP_FMAX2 = 0, QP_P = 1, QP_VV = 2, QP_FF = 3, QP_FRIG = 4, QP_XRIG = 7, Q
 enum { MODE_CLOSE = 1, MODE_OPEN = 2, MODE_KIN = 4 };  // KIN: kinetic energy only
 enum { ROLE_FIXED = 0, ROLE_MOBILE = 1, ROLE_RIGID = 2 };
 
+// Per-atom record read by the pair sweep: fixed-point position (w = type |
+// role << 8) and, in the split form, r - r_O in FP32; one 32-byte sector.
+struct __align__(32) AtomRec {
+    int4 p;
+    float4 d;
+};
+
 struct RepDev {
     int dim, n, atom0, tile0, ntile, nrig, m_exp, rep_id;
     int cell0, ncell, vert, pad0;
@@ -62,6 +72,13 @@ struct RepDev {
     double open_lim;             // escape bound |x - origin| on the open axis
     double kr_n;                 // k / n_rig (spring Hessian per rigid atom)
     float kr_nf, c_ouf, s_ouf, pad1;
+    // exact squared distances: all axes share one fixed-point unit u (the open
+    // axis counts 2^zshift units per step); u^2 = lsb2_hi + lsb2_lo
+    int exact_r2, zshift;
+    float lsb2_hi, lsb2_lo;
+    float lsb_rel[3];            // (unit - fl32(unit)) / fl32(unit) per axis
+    float pad2;
+    float r0sq_hi[2][2], r0sq_lo[2][2];  // 2^(1/3) sigma_ab^2 (LJ minimum, squared) as hi + lo
 };
 
 struct RepState {
@@ -84,7 +101,7 @@ struct Scal {
 
 struct Dev {
     int nrep, ntile, natom, maxnb, cell_cap, ncell, prec, bias_on, block;
-    int q_method, pad0;
+    int q_method, max_cells;        // max_cells: largest cell count of one replica
     double dt, rc2, rl2, half_skin2, q_ftol, q_step, q_theta;
     float rc2f, rl2_lo_f, rl2_hi_f, half_skin2_f;
     uint32_t seed_lo, seed_hi;
@@ -95,13 +112,15 @@ struct Dev {
     double *part, *kpart;
     dbl4 *x, *xo;
     dbl4 *v64, *f64, *h64, *dr64;
-    float4 *v32, *f32, *h32, *dr32;
-    int4 *pfix, *pfixb;
+    float4 *v32, *f32, *h32;
+    AtomRec *rec;                // fixed-point position + FP32 r - r_O
+    int4 *pfixb;
     int *cellid, *nnb, *nbr, *cell_cnt, *cell_atoms;
     int *rebuild;                // per replica: list rebuild requested
     int *err;                    // [0] first error code, [1] atom, [2] replica
     unsigned int *bar;           // per replica barrier counters (persistent driver)
     unsigned long long *qdisp;   // per replica max |x_q - r_O|^2 (bits of the double)
+    const int *orig;             // per slot: index of the atom in its replica's input
 };
 
 // ------------------------------------------------------------------ helpers
@@ -193,6 +212,21 @@ __device__ __forceinline__ double exact_r2(const RepDev &R, dbl4 a, dbl4 b) {
 
 __device__ __forceinline__ double mi64(const RepDev &R, int a, double d) {
     return R.periodic[a] ? d - R.L[a] * rint(d * R.invL[a]) : d;
+}
+
+// r^2_exact - r2f for a pair with integer separations (ix, iy, iz) in the
+// common fixed-point unit: q = sum of squares, the open axis scaled by
+// 2^zshift, is exact in 64 bits; q = qh + ql with qh = fl(q) and ql exact; then
+// u^2 q - r2f = fma(u2h, qh, -r2f) + u2h ql + u2l qh  (to ~2^-40 r^2).
+__device__ __forceinline__ float r2_residual(const RepDev &R, int ix, int iy, int iz, float r2f) {
+    // the open (vertical) axis counts 2^zshift units per fixed-point step
+    const long long sy = (long long)iy << (R.vert == 1 ? R.zshift : 0);
+    const long long sz = (long long)iz << (R.vert == 2 ? R.zshift : 0);
+    const unsigned long long q = (unsigned long long)((long long)ix * ix) + (unsigned long long)(sy * sy) +
+                                 (unsigned long long)(sz * sz);
+    const float qh = __ull2float_rn(q);
+    const float ql = (float)(long long)(q - __float2ull_rn(qh));
+    return fmaf(R.lsb2_hi, qh, -r2f) + fmaf(R.lsb2_hi, ql, R.lsb2_lo * qh);
 }
 
 template <typename T>

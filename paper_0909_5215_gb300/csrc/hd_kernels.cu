@@ -49,25 +49,25 @@ __global__ void k_init(Dev D, const int *draw_vel) {
     const int i = D.tile_start[t] + threadIdx.x;
     const RepDev &R = D.rep[r];
     dbl4 x = D.x[i], xo = D.xo[i];
-    int4 p = D.pfix[i];  // w (type | role << 8) preset by the host
+    int4 p = D.rec[i].p;  // w (type | role << 8) preset by the host
     p = fix_pos(R, x, p.w);
-    D.pfix[i] = p;
+    D.rec[i].p = p;
     D.pfixb[i] = p;
     const int role = (p.w >> 8) & 0xff;
     if (D.prec == HD_FP64)
         D.dr64[i] = make_dbl4(x.x - xo.x, x.y - xo.y, x.z - xo.z, 0.0);
     else
-        D.dr32[i] = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
+        D.rec[i].d = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
     if (draw_vel[r]) {
         double v0 = 0, v1 = 0, v2 = 0;
         if (role == ROLE_MOBILE) {
             const double sd = sqrt(R.kT);
             double z0, z1, z2, z3;
-            normals64(philox_draw(D, D.st[r].step, i - R.atom0, R.rep_id, 2), z0, z1);
+            normals64(philox_draw(D, D.st[r].step, D.orig[i], R.rep_id, 2), z0, z1);
             v0 = sd * z0;
             v1 = sd * z1;
             if (R.dim == 3) {
-                normals64(philox_draw(D, D.st[r].step, i - R.atom0, R.rep_id, 3), z2, z3);
+                normals64(philox_draw(D, D.st[r].step, D.orig[i], R.rep_id, 3), z2, z3);
                 v2 = sd * z2;
             }
         }
@@ -89,7 +89,7 @@ __global__ void k_bin(Dev D) {
     if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
     const int i = D.tile_start[t] + threadIdx.x;
     const RepDev &R = D.rep[r];
-    const int4 p = D.pfix[i];
+    const int4 p = D.rec[i].p;
     const int cx = cell_axis(R, 0, p.x), cy = cell_axis(R, 1, p.y), cz = cell_axis(R, 2, p.z);
     D.cellid[i] = cx | (cy << 10) | (cz << 20);
     const int c = R.cell0 + (cz * R.nc[1] + cy) * R.nc[0] + cx;
@@ -97,6 +97,28 @@ __global__ void k_bin(Dev D) {
     if (slot < D.cell_cap) D.cell_atoms[(size_t)c * D.cell_cap + slot] = i;
     else set_err(D, HD_ERR_OVERFLOW, i, r);
     D.pfixb[i] = p;
+}
+
+// Each cell's atom list in ascending slot order (one thread per cell).  With
+// atoms stored cell-major, walking the neighbour cells in ascending cell
+// order then yields candidates in (almost) ascending j.
+__global__ void k_cellsort(Dev D) {
+    const int r = blockIdx.y;
+    if (!D.rebuild[r]) return;
+    const RepDev &R = D.rep[r];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= R.ncell) return;
+    int *a = D.cell_atoms + (size_t)(R.cell0 + c) * D.cell_cap;
+    const int m = min(D.cell_cnt[R.cell0 + c], D.cell_cap);
+    for (int k = 1; k < m; ++k) {
+        const int v = a[k];
+        int q = k;
+        while (q > 0 && a[q - 1] > v) {
+            a[q] = a[q - 1];
+            --q;
+        }
+        a[q] = v;
+    }
 }
 
 // Row i = every j != i whose FP64 minimum-image squared distance is below
@@ -109,7 +131,7 @@ __global__ void __launch_bounds__(128) k_nlist(Dev D) {
     if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
     const int i = D.tile_start[t] + threadIdx.x;
     const RepDev &R = D.rep[r];
-    const int4 pi = D.pfix[i];
+    const int4 pi = D.rec[i].p;
     const dbl4 xi = D.x[i];
     const int cid = D.cellid[i];
     const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
@@ -127,6 +149,13 @@ __global__ void __launch_bounds__(128) k_nlist(Dev D) {
                 else if (c < 0 || c >= nc) continue;
                 cs[a][ncs[a]++] = c;
             }
+            // ascending (a periodic wrap puts nc-1 before 0 and 1)
+            for (int u = 1; u < ncs[a]; ++u)
+                for (int w = u; w > 0 && cs[a][w - 1] > cs[a][w]; --w) {
+                    const int tmp = cs[a][w];
+                    cs[a][w] = cs[a][w - 1];
+                    cs[a][w - 1] = tmp;
+                }
         }
     }
     const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
@@ -143,7 +172,7 @@ __global__ void __launch_bounds__(128) k_nlist(Dev D) {
                 for (int k = 0; k < m; ++k) {
                     const int j = ca[k];
                     if (j == i) continue;
-                    const int4 pj = D.pfix[j];
+                    const int4 pj = D.rec[j].p;
                     const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
                     const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
                     const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
@@ -217,7 +246,7 @@ __global__ void __launch_bounds__(256) k_pair64(Dev D) {
             }
         }
     }
-    const int role = act ? ((D.pfix[i].w >> 8) & 0xff) : -1;
+    const int role = act ? ((D.rec[i].p.w >> 8) & 0xff) : -1;
     if (!Q && role == ROLE_RIGID) {
         hx += R.kr_n * dri.x;
         if (R.dim == 3) hy += R.kr_n * dri.y;
@@ -259,7 +288,17 @@ __global__ void __launch_bounds__(256) k_pair64(Dev D) {
 }
 
 // Split form: positions are differenced exactly in 32-bit fixed point, the
-// pair arithmetic is FP32; per-tile sums are carried in FP64.
+// pair arithmetic is FP32; per-tile sums are carried in FP64.  Near the LJ
+// minimum the force holds the cancelling factor (2 s^6 - 1); it is evaluated
+// as (1 + t)^3 - 1 = t (3 + 3t + t^2) with t = (r_0^2 - r^2) / r^2, r_0^2 =
+// 2^(1/3) sigma^2, and r^2 carried as hi + lo from the exact integer sum of
+// squares, so the FP32 result is accurate relative to the force itself.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <bool Q>
 __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     const int t = blockIdx.x, r = D.tile_rep[t];
@@ -267,46 +306,64 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     const RepDev &R = D.rep[r];
     const bool act = threadIdx.x < D.tile_n[t];
     const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
-    const int4 pi = D.pfix[i];
+    const AtomRec ai = D.rec[i];
+    const int4 pi = ai.p;
     const int ti = pi.w & 1;
-    const float4 dri = Q ? make_float4(0.f, 0.f, 0.f, 0.f) : D.dr32[i];
+    const float4 dri = Q ? make_float4(0.f, 0.f, 0.f, 0.f) : ai.d;
     const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
     const float e0 = R.epsf[ti][0], e1 = R.epsf[ti][1];
-    const float s0 = R.sig2f[ti][0], s1 = R.sig2f[ti][1];
     const float h0 = R.shiftf[ti][0], h1 = R.shiftf[ti][1];
+    const float q0h = R.r0sq_hi[ti][0], q1h = R.r0sq_hi[ti][1];
+    const float q0l = R.r0sq_lo[ti][0], q1l = R.r0sq_lo[ti][1];
     const float rc2 = D.rc2f;
+    const bool exact = R.exact_r2 != 0;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
     const int nn = act ? D.nnb[i] : 0;
     const int *nb = D.nbr + i;
+    const size_t stride = (size_t)D.natom;
+    // software pipeline: the next neighbour's record is in flight while this one is used
+    int jn = nn > 0 ? __ldg(nb) : i;
+    AtomRec an = D.rec[jn];
     for (int k = 0; k < nn; ++k) {
-        const int j = __ldg(nb + (size_t)k * D.natom);
-        const int4 pj = D.pfix[j];
-        const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
-        const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
-        const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
+        const AtomRec aj = an;
+        if (k + 1 < nn) {
+            jn = __ldg(nb + (size_t)(k + 1) * stride);
+            an = D.rec[jn];
+        }
+        const int4 pj = aj.p;
+        const int ix = (int)((unsigned)pi.x - (unsigned)pj.x);
+        const int iy = (int)((unsigned)pi.y - (unsigned)pj.y);
+        const int iz = (int)((unsigned)pi.z - (unsigned)pj.z);
+        const float dx = (float)ix * lx, dy = (float)iy * ly, dz = (float)iz * lz;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (r2 < rc2) {
             const int tj = pj.w & 1;
             const float eps = tj ? e1 : e0;
-            const float ir2 = __frcp_rn(r2);
-            const float s2 = (tj ? s1 : s0) * ir2;
-            const float s6 = s2 * s2 * s2;
-            const float fr = 24.f * eps * ir2 * s6 * (2.f * s6 - 1.f);
+            const float ir2 = rcp_approx(r2);
+            const float r2lo = exact ? r2_residual(R, ix, iy, iz, r2) : 0.f;
+            const float tt = (((tj ? q1h : q0h) - r2) + ((tj ? q1l : q0l) - r2lo)) * ir2;
+            const float u = 1.f + tt;
+            const float s6 = 0.5f * u * u * u;
+            const float w = tt * fmaf(tt, tt + 3.f, 3.f);          // 2 s^6 - 1
+            const float fr = 24.f * eps * ir2 * s6 * w;
             fx = fmaf(fr, dx, fx);
             fy = fmaf(fr, dy, fy);
             fz = fmaf(fr, dz, fz);
-            e += 0.5f * (4.f * eps * s6 * (s6 - 1.f) - (tj ? h1 : h0));
+            e = fmaf(0.5f, fmaf(4.f * eps * s6, s6 - 1.f, -(tj ? h1 : h0)), e);
             if (!Q) {
-                const float4 drj = D.dr32[j];
-                const float ux = dri.x - drj.x, uy = dri.y - drj.y, uz = dri.z - drj.z;
+                const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
                 const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-                const float B = 96.f * eps * ir2 * ir2 * s6 * (7.f * s6 - 2.f) * rdu;
+                const float B = 96.f * eps * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
                 hx += fmaf(B, dx, -fr * ux);
                 hy += fmaf(B, dy, -fr * uy);
                 hz += fmaf(B, dz, -fr * uz);
             }
         }
     }
+    // undo the FP32 rounding of the per-axis fixed-point unit (uniform per axis)
+    fx = fmaf(fx, R.lsb_rel[0], fx);
+    fy = fmaf(fy, R.lsb_rel[1], fy);
+    fz = fmaf(fz, R.lsb_rel[2], fz);
     const int role = act ? ((pi.w >> 8) & 0xff) : -1;
     if (!Q && role == ROLE_RIGID) {
         hx += R.kr_nf * dri.x;
@@ -461,7 +518,7 @@ __global__ void k_obs(Dev D) {
 // Mobile atoms only; rigid atoms follow the body velocity; fixed atoms stay.
 __device__ __forceinline__ void post_move(const Dev &D, const RepDev &R, int r, int i, dbl4 x, int4 p) {
     const int4 q = fix_pos(R, x, p.w);
-    D.pfix[i] = q;
+    D.rec[i].p = q;
     const int4 b = D.pfixb[i];
     const float ex = (float)(int)((unsigned)q.x - (unsigned)b.x) * R.fx_lsb[0];
     const float ey = (float)(int)((unsigned)q.y - (unsigned)b.y) * R.fx_lsb[1];
@@ -478,7 +535,7 @@ __global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
     const Scal &C = D.sc[r];
     const bool act = threadIdx.x < D.tile_n[t];
     const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
-    const int4 p = D.pfix[i];
+    const int4 p = D.rec[i].p;
     const int role = act ? ((p.w >> 8) & 0xff) : ROLE_FIXED;
     double kin = 0.0;
     if (role != ROLE_FIXED) {
@@ -506,11 +563,11 @@ __global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
                 x.y += 0.5 * h * v.y;
                 if (three) x.z += 0.5 * h * v.z;
                 double n0, n1, n2, n3;
-                normals64(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 0), n0, n1);
+                normals64(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
                 v.x = R.c_ou * v.x + R.s_ou * n0;
                 v.y = R.c_ou * v.y + R.s_ou * n1;
                 if (three) {
-                    normals64(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 1), n2, n3);
+                    normals64(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
                     v.z = R.c_ou * v.z + R.s_ou * n2;
                 }
                 x.x += 0.5 * h * v.x;
@@ -549,7 +606,7 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
     const Scal &C = D.sc[r];
     const bool act = threadIdx.x < D.tile_n[t];
     const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
-    const int4 p = D.pfix[i];
+    const int4 p = D.rec[i].p;
     const int role = act ? ((p.w >> 8) & 0xff) : ROLE_FIXED;
     float kin = 0.f;
     if (role != ROLE_FIXED) {
@@ -557,7 +614,7 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
         float4 v = D.v32[i];
         dbl4 x = D.x[i];
         if (role == ROLE_MOBILE) {
-            const float4 F = D.f32[i], H = D.h32[i], dr = D.dr32[i];
+            const float4 F = D.f32[i], H = D.h32[i], dr = D.rec[i].d;
             const float ca = (float)C.ca, cb = (float)C.cb;
             const float Fx = fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
             const float Fy = fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
@@ -576,11 +633,11 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
                 if (three) v.z = fmaf(hh, Fz, v.z);
                 const float ax = v.x, ay = v.y, az = v.z;
                 float n0, n1, n2, n3;
-                normals32(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 0), n0, n1);
+                normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
                 v.x = fmaf(R.c_ouf, v.x, R.s_ouf * n0);
                 v.y = fmaf(R.c_ouf, v.y, R.s_ouf * n1);
                 if (three) {
-                    normals32(philox_draw(D, C.step_cur, i - R.atom0, R.rep_id, 1), n2, n3);
+                    normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
                     v.z = fmaf(R.c_ouf, v.z, R.s_ouf * n2);
                 }
                 x.x += (double)(hh * (ax + v.x));
@@ -604,7 +661,7 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
         if (mode & MODE_OPEN) {
             D.x[i] = x;
             const dbl4 xo = D.xo[i];
-            D.dr32[i] = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
+            D.rec[i].d = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
             post_move(D, R, r, i, x, p);
         }
     }
@@ -634,7 +691,7 @@ __global__ void k_qinit(Dev Q, Dev M) {
     if (threadIdx.x >= Q.tile_n[t]) return;
     const int i = Q.tile_start[t] + threadIdx.x;
     Q.x[i] = M.x[i];
-    Q.pfix[i] = M.pfix[i];
+    Q.rec[i].p = M.rec[i].p;
     if (Q.prec == HD_FP64) Q.v64[i] = make_dbl4(0, 0, 0, 0);
     else Q.v32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -778,7 +835,7 @@ __global__ void __launch_bounds__(256) k_qupdate(Dev D) {
     if (threadIdx.x >= D.tile_n[t]) return;
     const int i = D.tile_start[t] + threadIdx.x;
     const RepDev &R = D.rep[r];
-    const int4 p = D.pfix[i];
+    const int4 p = D.rec[i].p;
     const int role = (p.w >> 8) & 0xff;
     if (role == ROLE_FIXED) return;
     if (D.prec == HD_FP64) {
@@ -816,7 +873,7 @@ __global__ void k_adopt(Dev Q, Dev M, const int *adopt) {
     M.xo[i] = make_dbl4(q.x, q.y, q.z, 0.0);
     const dbl4 x = M.x[i];
     if (M.prec == HD_FP64) M.dr64[i] = make_dbl4(x.x - q.x, x.y - q.y, x.z - q.z, 0.0);
-    else M.dr32[i] = make_float4((float)(x.x - q.x), (float)(x.y - q.y), (float)(x.z - q.z), 0.f);
+    else M.rec[i].d = make_float4((float)(x.x - q.x), (float)(x.y - q.y), (float)(x.z - q.z), 0.f);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -828,6 +885,7 @@ void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s) {
 void launch_rebuild(const Dev &D, cudaStream_t s) {
     k_cell_clear<<<D.nrep, 256, 0, s>>>(D);
     k_bin<<<D.ntile, nthr(D), 0, s>>>(D);
+    k_cellsort<<<dim3((D.max_cells + 127) / 128, D.nrep), 128, 0, s>>>(D);
     k_nlist<<<D.ntile, nthr(D), 0, s>>>(D);
 }
 void launch_pair(const Dev &D, bool quench, cudaStream_t s) {
