@@ -34,7 +34,7 @@ struct Plan {
     size_t o_rep, o_st, o_sc, o_trep, o_tstart, o_tn, o_part, o_qpart, o_kpart;
     size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
-    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig;
+    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff;
 };
 
 size_t take(size_t &cur, size_t bytes) {
@@ -126,14 +126,19 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                 bool same = true;
                 for (int q = 0; q < d.dim - 1; ++q) same &= d.box[q] == d.box[0];
                 double span;
-                if (same) {
+                if (same && d.box[0] > 2.0 * (p->rc + 0.5)) {
                     int k = 0;
                     span = d.box[0];
                     while (span < need) { span *= 2.0; ++k; }
                     R.exact_r2 = 1;
                     R.zshift = k;
-                    R.lsb2_hi = (float)((d.box[0] / 4294967296.0) * (d.box[0] / 4294967296.0));
-                    R.lsb2_lo = (float)((d.box[0] / 4294967296.0) * (d.box[0] / 4294967296.0) - (double)R.lsb2_hi);
+                    R.shift_y = a == 1 ? k : 0;
+                    R.shift_z = a == 2 ? k : 0;
+                    const double u = d.box[0] / 4294967296.0, u2 = u * u;
+                    R.u2_42 = (float)(u2 * 4398046511104.0);
+                    R.u2lo_42 = (float)(u2 * 4398046511104.0 - (double)R.u2_42);
+                    R.u2_21 = (float)(u2 * 2097152.0);
+                    R.u2_0 = (float)u2;
                 } else {
                     span = 64.0;
                     while (span < need) span *= 2.0;
@@ -239,7 +244,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_x = take(cur, N * sizeof(dbl4));
     P.o_xo = take(cur, N * sizeof(dbl4));
     P.o_xq = take(cur, N * sizeof(dbl4));
-    P.o_v = take(cur, N * v4);
+    P.o_v = take(cur, N * sizeof(dbl4));     // velocities are FP64 in both forms
     P.o_vq = take(cur, N * v4);
     P.o_f = take(cur, N * v4);
     P.o_fq = take(cur, N * v4);
@@ -262,6 +267,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_drawvel = take(cur, R * 4);
     P.o_adopt = take(cur, R * 4);
     P.o_orig = take(cur, N * 4);
+    P.o_rboff = take(cur, (R + 1) * 4);
     P.bytes = (cur + ALIGN - 1) / ALIGN * ALIGN;
     return true;
 }
@@ -409,13 +415,12 @@ void fill_dev(hd_ctx *c) {
     D.kpart = at<double>(b, P.o_kpart);
     D.x = at<dbl4>(b, P.o_x);
     D.xo = at<dbl4>(b, P.o_xo);
+    D.v64 = at<dbl4>(b, P.o_v);
     if (P.prec == HD_FP64) {
-        D.v64 = at<dbl4>(b, P.o_v);
         D.f64 = at<dbl4>(b, P.o_f);
         D.h64 = at<dbl4>(b, P.o_h);
         D.dr64 = at<dbl4>(b, P.o_dr);
     } else {
-        D.v32 = at<float4>(b, P.o_v);
         D.f32 = at<float4>(b, P.o_f);
         D.h32 = at<float4>(b, P.o_h);
     }
@@ -431,6 +436,15 @@ void fill_dev(hd_ctx *c) {
     D.bar = at<unsigned int>(b, P.o_bar);
     D.qdisp = at<unsigned long long>(b, P.o_qdisp);
     D.orig = at<int>(b, P.o_orig);
+    D.rb_off = at<int>(b, P.o_rboff);
+    D.nl_pow2 = 32;
+    while (D.nl_pow2 < P.maxnb) D.nl_pow2 <<= 1;
+    {
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        D.nl_grid = nsm * 4;
+    }
     // quench view: the copy of the positions and its own velocity, force,
     // fixed-point image, rebuild flags and tile sums
     Dev &Q = c->Q;
@@ -459,6 +473,8 @@ void set_scalars(Dev &D, const hd_params *p) {
     D.rc2f = (float)D.rc2;
     D.rl2_lo_f = (float)(D.rl2 * (1.0 - 1.0 / 4096.0));
     D.rl2_hi_f = (float)(D.rl2 * (1.0 + 1.0 / 4096.0));
+    D.rc2_lo_f = (float)(D.rc2 * (1.0 - 1.0 / 4096.0));
+    D.rc2_hi_f = (float)(D.rc2 * (1.0 + 1.0 / 4096.0));
     D.half_skin2_f = (float)(D.half_skin2 * (1.0 - 1e-4));
     D.seed_lo = (uint32_t)p->seed;
     D.seed_hi = (uint32_t)(p->seed >> 32);
@@ -492,7 +508,7 @@ void queue_step(hd_ctx *c, int mode, std::vector<hd_ctx::Span> *sink) {
     { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, c->s); }
     { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, mode, c->s); }
     { Timed t(c, sink, T_UPDATE); launch_update(c->D, mode, c->s); }
-    c->launches += 7;
+    c->launches += 8;
 }
 
 void queue_steps(hd_ctx *c, int n, std::vector<hd_ctx::Span> *sink) {
@@ -509,7 +525,7 @@ hd_status refresh_md(hd_ctx *c, bool relist) {
         CK(cudaMemcpyAsync(c->D.rebuild, two.data(), two.size() * 4, cudaMemcpyHostToDevice, c->s));
         c->h2d += (long long)two.size() * 4;
         launch_rebuild(c->D, c->s);
-        c->launches += 4;
+        c->launches += 5;
         CK(cudaStreamSynchronize(c->s));
     }
     launch_pair(c->D, false, c->s);
@@ -554,7 +570,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     // host staging
     std::vector<dbl4> hx(N), hxo(N);
     std::vector<AtomRec> hp(N);
-    std::vector<char> hv(N * (P.prec == HD_FP64 ? sizeof(dbl4) : sizeof(float4)));
+    std::vector<char> hv(N * sizeof(dbl4));
     std::vector<RepState> hst(P.nrep);
     std::vector<int> draw(P.nrep), two(P.nrep, 2);
     memset(hst.data(), 0, hst.size() * sizeof(RepState));
@@ -583,8 +599,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
             if (d.vel && d.role[i] != 0)
                 for (int a = 0; a < 3; ++a) v[a] = d.vel[3 * i + a];
             if (d.dim == 2) v[2] = 0.0;
-            if (P.prec == HD_FP64) reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
-            else reinterpret_cast<float4 *>(hv.data())[a0 + sl] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+            reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
         }
     }
     if (upload_reps(c) != HD_OK) return c->status;
@@ -606,7 +621,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     launch_scalar(c->D, 0, c->s);
     launch_update(c->D, MODE_KIN, c->s);  // kinetic energy of the initial velocities
     launch_obs(c->D, c->s);
-    c->launches += 9;
+    c->launches += 10;
     CK(cudaGetLastError());
     c->qdisp.assign(P.nrep, 0.0);
     c->qflag.assign(P.nrep, 0);
@@ -693,7 +708,7 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     }
     CK(cudaGraphLaunch(it->second, c->s));
     if (c->timing) c->graph_pending.push_back(key);
-    c->launches += 2 + 7LL * n_steps;
+    c->launches += 2 + 8LL * n_steps;
     return HD_OK;
 }
 
@@ -741,7 +756,7 @@ hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double ste
         if (qg) CK(cudaGraphLaunch(qg, c->s));
         else
             for (int k = 0; k < chunk; ++k) launch_qiter(Q, max_iter, c->s);
-        c->launches += 7LL * chunk;
+        c->launches += 8LL * chunk;
         done_iters += chunk;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(st.data(), c->D.st, R * sizeof(RepState), cudaMemcpyDeviceToHost, c->s));
@@ -837,7 +852,7 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         return vec3(c->Q.x, true, -1);
     case HD_FIELD_VEL:
         if (!need(n * 24)) break;
-        return vec3(c->ws + P.o_v, f64, -1);
+        return vec3(c->ws + P.o_v, true, -1);
     case HD_FIELD_FORCE:
         if (!need(n * 24)) break;
         return vec3(c->ws + P.o_f, f64, -1);

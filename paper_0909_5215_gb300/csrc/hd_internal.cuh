@@ -74,8 +74,8 @@ struct RepDev {
     float kr_nf, c_ouf, s_ouf, pad1;
     // exact squared distances: all axes share one fixed-point unit u (the open
     // axis counts 2^zshift units per step); u^2 = lsb2_hi + lsb2_lo
-    int exact_r2, zshift;
-    float lsb2_hi, lsb2_lo;
+    int exact_r2, zshift, shift_y, shift_z;
+    float u2_42, u2_21, u2_0, u2lo_42;     // u^2 2^42, u^2 2^21, u^2 (FP32) and the low part of u^2 2^42
     float lsb_rel[3];            // (unit - fl32(unit)) / fl32(unit) per axis
     float pad2;
     float r0sq_hi[2][2], r0sq_lo[2][2];  // 2^(1/3) sigma_ab^2 (LJ minimum, squared) as hi + lo
@@ -104,6 +104,7 @@ struct Dev {
     int q_method, max_cells;        // max_cells: largest cell count of one replica
     double dt, rc2, rl2, half_skin2, q_ftol, q_step, q_theta;
     float rc2f, rl2_lo_f, rl2_hi_f, half_skin2_f;
+    float rc2_lo_f, rc2_hi_f;    // rc^2 (1 -+ 2^-12): band decided in FP64
     uint32_t seed_lo, seed_hi;
     const RepDev *rep;
     RepState *st;
@@ -121,6 +122,8 @@ struct Dev {
     unsigned int *bar;           // per replica barrier counters (persistent driver)
     unsigned long long *qdisp;   // per replica max |x_q - r_O|^2 (bits of the double)
     const int *orig;             // per slot: index of the atom in its replica's input
+    int *rb_off;                 // [nrep + 1] compacted atom offsets of rebuilding replicas
+    int nl_pow2, nl_grid;        // neighbour-row buffer (power of two >= maxnb), k_nlist CTAs
 };
 
 // ------------------------------------------------------------------ helpers
@@ -169,13 +172,25 @@ __device__ __forceinline__ void normals64(uint4 w, double &n0, double &n1) {
     n0 = rad * c;
     n1 = rad * s;
 }
+// FP32 Box-Muller from the same 52-bit uniforms u = (k + 1/2) 2^-52: u is
+// split into its top 24 bits (head, exact in FP32) and the rest (tail); the
+// tails enter to first order (log u = log fl(u) + (u - fl(u)) / fl(u), and
+// the angle is rotated by 2 pi tail), so the normals are FP32-accurate with
+// respect to the FP64 draw rather than to a 24-bit uniform.
 __device__ __forceinline__ void normals32(uint4 w, float &n0, float &n1) {
-    float u1 = unif32(w.x, w.y), u2 = unif32(w.z, w.w);
-    float rad = sqrtf(-2.0f * logf(u1));
+    const float h1 = (float)(w.x >> 8) * 0x1p-24f;
+    const float t1 = ((float)((((w.x >> 6) & 3u) << 26) | (w.y >> 6)) + 0.5f) * 0x1p-52f;
+    const float u1 = h1 + t1;
+    const float r1 = (h1 - u1) + t1;                      // u1 - fl(u1), exact to FP32
+    const float l = logf(u1) + __fdividef(r1, u1);
+    const float rad = sqrtf(-2.0f * l);
+    const float h2 = (float)(w.z >> 8) * 0x1p-24f;
+    const float t2 = ((float)((((w.z >> 6) & 3u) << 26) | (w.w >> 6)) + 0.5f) * 0x1p-52f;
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    n0 = rad * c;
-    n1 = rad * s;
+    sincospif(2.0f * h2, &s, &c);
+    const float da = 6.28318530717958648f * t2;
+    n0 = rad * fmaf(-s, da, c);
+    n1 = rad * fmaf(c, da, s);
 }
 
 // Fixed-point image of one coordinate.
@@ -201,12 +216,16 @@ __device__ __forceinline__ int cell_axis(const RepDev &R, int a, int q) {
 }
 
 // The oracle's squared distance, op for op: minimum image per axis as
-// d - L rint(d / L), then ((dx dx + dy dy) + dz dz), every operation rounded.
+// d - L k with k the nearest integer to d / L, then ((dx dx + dy dy) + dz dz),
+// every operation rounded.  k is taken as rint(d * (1/L)): for any pair
+// within the list radius (L >= 3 (rc + skin)) d / L is far from a half
+// integer, so k, and with it every rounded operation after it, is the same
+// as the oracle's rint(d / L).
 __device__ __forceinline__ double exact_r2(const RepDev &R, dbl4 a, dbl4 b) {
     double d0 = __dsub_rn(a.x, b.x), d1 = __dsub_rn(a.y, b.y), d2 = __dsub_rn(a.z, b.z);
-    if (R.periodic[0]) d0 = __dsub_rn(d0, __dmul_rn(R.L[0], rint(__ddiv_rn(d0, R.L[0]))));
-    if (R.periodic[1]) d1 = __dsub_rn(d1, __dmul_rn(R.L[1], rint(__ddiv_rn(d1, R.L[1]))));
-    if (R.periodic[2]) d2 = __dsub_rn(d2, __dmul_rn(R.L[2], rint(__ddiv_rn(d2, R.L[2]))));
+    if (R.periodic[0]) d0 = __dsub_rn(d0, __dmul_rn(R.L[0], rint(d0 * R.invL[0])));
+    if (R.periodic[1]) d1 = __dsub_rn(d1, __dmul_rn(R.L[1], rint(d1 * R.invL[1])));
+    if (R.periodic[2]) d2 = __dsub_rn(d2, __dmul_rn(R.L[2], rint(d2 * R.invL[2])));
     return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
 }
 
@@ -214,19 +233,32 @@ __device__ __forceinline__ double mi64(const RepDev &R, int a, double d) {
     return R.periodic[a] ? d - R.L[a] * rint(d * R.invL[a]) : d;
 }
 
-// r^2_exact - r2f for a pair with integer separations (ix, iy, iz) in the
-// common fixed-point unit: q = sum of squares, the open axis scaled by
-// 2^zshift, is exact in 64 bits; q = qh + ql with qh = fl(q) and ql exact; then
-// u^2 q - r2f = fma(u2h, qh, -r2f) + u2h ql + u2l qh  (to ~2^-40 r^2).
-__device__ __forceinline__ float r2_residual(const RepDev &R, int ix, int iy, int iz, float r2f) {
-    // the open (vertical) axis counts 2^zshift units per fixed-point step
-    const long long sy = (long long)iy << (R.vert == 1 ? R.zshift : 0);
-    const long long sz = (long long)iz << (R.vert == 2 ? R.zshift : 0);
-    const unsigned long long q = (unsigned long long)((long long)ix * ix) + (unsigned long long)(sy * sy) +
-                                 (unsigned long long)(sz * sz);
-    const float qh = __ull2float_rn(q);
-    const float ql = (float)(long long)(q - __float2ull_rn(qh));
-    return fmaf(R.lsb2_hi, qh, -r2f) + fmaf(R.lsb2_hi, ql, R.lsb2_lo * qh);
+// Exact squared distance of an interacting pair as FP32 hi + lo, from its
+// integer separations (ix, iy, iz) in the common fixed-point unit u (the open
+// axis counts 2^zshift units per step).  q = sum of squares is exact in 64-bit
+// integers (three 32x32->64 multiply-adds); q is cut into three 21-bit pieces,
+// each turned into an exact float by the 2^23 bias trick, and
+// u^2 q = hi + lo with hi the FP32 rounding of u^2 q and lo the remainder
+// (TwoProduct by FMA, Fast2Sum).  Integer and FP32 pipes only.
+__device__ __forceinline__ float exact_f23(unsigned int p) {
+    return __int_as_float(0x4B000000u | p) - 8388608.0f;  // exact for p < 2^23
+}
+__device__ __forceinline__ void r2_split(const RepDev &R, int ix, int iy, int iz, float &hi, float &lo) {
+    const int sy = iy << R.shift_y, sz = iz << R.shift_z;
+    unsigned long long q = (unsigned long long)((long long)ix * (long long)ix);
+    q += (unsigned long long)((long long)sy * (long long)sy);
+    q += (unsigned long long)((long long)sz * (long long)sz);
+    const float f0 = exact_f23((unsigned int)q & 0x1FFFFFu);
+    const float f1 = exact_f23((unsigned int)(q >> 21) & 0x1FFFFFu);
+    const float f2 = exact_f23((unsigned int)(q >> 42));
+    // hi = fl(u^2 q): the top piece plus the middle one (Fast2Sum, |a| >= |b|);
+    // lo = both rounding errors plus the small terms
+    const float a = f2 * R.u2_42;
+    const float ea = fmaf(f2, R.u2_42, -a);
+    const float b = f1 * R.u2_21;
+    hi = a + b;
+    const float eb = (a - hi) + b;
+    lo = (ea + eb) + fmaf(f0, R.u2_0, f2 * R.u2lo_42);
 }
 
 template <typename T>

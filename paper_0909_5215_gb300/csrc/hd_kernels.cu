@@ -40,6 +40,70 @@ __device__ __forceinline__ void cta_reduce(double (&v)[NV], double *out, int max
     __syncthreads();
 }
 
+// Tile sums of the split form: slots [0, nf) are FP32 per-atom values summed
+// in FP32 within each warp; xr (rigid positions, FP64) go to slots
+// PART_XRIG..+2 when some lane holds a rigid atom.  Warp results are added in
+// FP64 in warp order.  Slots never written by a warp count as zero.
+__device__ __forceinline__ void tile_reduce_mixed(float (&v)[12], int nf, double (&xr)[3], bool anyrig,
+                                                  double *out) {
+    __shared__ double sm[32][NPART];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double wsum[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) wsum[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+        if (q < nf) wsum[q] = (double)warp_sum(v[q]);
+    if (anyrig)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) wsum[PART_XRIG + a] = warp_sum(xr[a]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NPART; ++q) sm[w][q] = wsum[q];
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        const int q = threadIdx.x;
+        double a = sm[0][q];
+        for (int k = 1; k < nw; ++k) a += sm[k][q];
+        out[q] = a;
+    }
+    __syncthreads();
+}
+
+// Quench tile sums: slot QP_FMAX2 is a max, the others sums (FP32 in warps).
+__device__ __forceinline__ void tile_reduce_quench(float (&v)[12], double (&xr)[3], bool anyrig, double *out) {
+    __shared__ double sm[32][NPART];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double wsum[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) wsum[q] = 0.0;
+    float m = v[QP_FMAX2];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    wsum[QP_FMAX2] = (double)m;
+    wsum[QP_P] = (double)warp_sum(v[QP_P]);
+    wsum[QP_VV] = (double)warp_sum(v[QP_VV]);
+    wsum[QP_FF] = (double)warp_sum(v[QP_FF]);
+    if (anyrig) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            wsum[QP_FRIG + a] = (double)warp_sum(v[QP_FRIG + a]);
+            wsum[QP_XRIG + a] = warp_sum(xr[a]);
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NPART; ++q) sm[w][q] = wsum[q];
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        const int q = threadIdx.x;
+        double a = sm[0][q];
+        for (int k = 1; k < nw; ++k) a = (q == QP_FMAX2) ? fmax(a, sm[k][q]) : a + sm[k][q];
+        out[q] = a;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- init
 // Fixed-point image, r - r_O, and (where asked) Maxwell-Boltzmann velocities
 // from Philox calls 2 and 3 at the current step.
@@ -71,8 +135,7 @@ __global__ void k_init(Dev D, const int *draw_vel) {
                 v2 = sd * z2;
             }
         }
-        if (D.prec == HD_FP64) D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
-        else D.v32[i] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+        D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
     }
 }
 
@@ -121,83 +184,107 @@ __global__ void k_cellsort(Dev D) {
     }
 }
 
-// Row i = every j != i whose FP64 minimum-image squared distance is below
-// (rc + skin)^2, ascending in j.  Candidates come from the 27 (9 in 2-D)
-// surrounding cells; an FP32 test on the exact integer differences decides
-// all but a thin band around the radius, where the FP64 test of the oracle
-// is repeated operation for operation.
-__global__ void __launch_bounds__(128) k_nlist(Dev D) {
-    const int t = blockIdx.x, r = D.tile_rep[t];
-    if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
-    const int i = D.tile_start[t] + threadIdx.x;
-    const RepDev &R = D.rep[r];
-    const int4 pi = D.rec[i].p;
-    const dbl4 xi = D.x[i];
-    const int cid = D.cellid[i];
-    const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
-    int cs[3][3], ncs[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int nc = R.nc[a];
-        ncs[a] = 0;
-        if (nc == 1) {
-            cs[a][ncs[a]++] = 0;
-        } else {
-            for (int d = -1; d <= 1; ++d) {
-                int c = ci[a] + d;
-                if (R.periodic[a]) c = (c + nc) % nc;
-                else if (c < 0 || c >= nc) continue;
-                cs[a][ncs[a]++] = c;
-            }
-            // ascending (a periodic wrap puts nc-1 before 0 and 1)
-            for (int u = 1; u < ncs[a]; ++u)
-                for (int w = u; w > 0 && cs[a][w - 1] > cs[a][w]; --w) {
-                    const int tmp = cs[a][w];
-                    cs[a][w] = cs[a][w - 1];
-                    cs[a][w - 1] = tmp;
-                }
-        }
+// Prefix of the atom counts of the replicas whose rebuild flag is set:
+// rb_off[r] = first compacted index of replica r, rb_off[nrep] = total.
+__global__ void k_rebuild_plan(Dev D) {
+    if (threadIdx.x != 0) return;
+    int tot = 0;
+    for (int r = 0; r < D.nrep; ++r) {
+        D.rb_off[r] = tot;
+        if (D.rebuild[r]) tot += D.rep[r].n;
     }
-    const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
-    int row[MAXNB_CAP];
-    int cnt = 0;
-    bool over = false;
+    D.rb_off[D.nrep] = tot;
+}
+
+// Row i = every j != i whose FP64 minimum-image squared distance is below
+// (rc + skin)^2.  One warp per atom: the 27 (9 in 2-D) surrounding cells are
+// walked in ascending cell order, the lanes testing one cell's list at a time
+// (an FP32 test on the exact integer differences decides all but a thin band
+// around the radius, where the oracle's FP64 test is repeated operation for
+// operation), and accepted j are packed in candidate order by ballot.  The
+// row order is thus a deterministic function of the cell lists (sorted by
+// k_cellsort); reads return each row ascending in j.
+__global__ void __launch_bounds__(256) k_nlist(Dev D) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    const int total = D.rb_off[D.nrep];
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
     const int cap = D.maxnb;
-    for (int iz = 0; iz < ncs[2]; ++iz)
-        for (int iy = 0; iy < ncs[1]; ++iy)
-            for (int ix = 0; ix < ncs[0]; ++ix) {
-                const int c = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
-                const int m = min(D.cell_cnt[c], D.cell_cap);
-                const int *ca = D.cell_atoms + (size_t)c * D.cell_cap;
-                for (int k = 0; k < m; ++k) {
-                    const int j = ca[k];
-                    if (j == i) continue;
-                    const int4 pj = D.rec[j].p;
-                    const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
-                    const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
-                    const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    bool in;
-                    if (r2 < D.rl2_lo_f) in = true;
-                    else if (r2 >= D.rl2_hi_f) in = false;
-                    else in = exact_r2(R, xi, D.x[j]) < D.rl2;
-                    if (!in) continue;
-                    if (cnt < cap) {
-                        int q = cnt;
-                        while (q > 0 && row[q - 1] > j) {
-                            row[q] = row[q - 1];
-                            --q;
+    for (int idx = blockIdx.x * (blockDim.x >> 5) + wib; idx < total; idx += nwarps) {
+        int lo = 0, hi = D.nrep - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (D.rb_off[mid] <= idx) lo = mid;
+            else hi = mid - 1;
+        }
+        const int r = lo;
+        const RepDev &R = D.rep[r];
+        const int i = R.atom0 + (idx - D.rb_off[r]);
+        const int4 pi = D.rec[i].p;
+        const dbl4 xi = D.x[i];
+        const int cid = D.cellid[i];
+        const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
+        int cs[3][3], ncs[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int nc = R.nc[a];
+            ncs[a] = 0;
+            if (nc == 1) {
+                cs[a][ncs[a]++] = 0;
+            } else {
+                // ascending: a periodic wrap puts nc-1 after 0 and 1
+                const int c0 = ci[a] - 1, c2 = ci[a] + 1;
+                if (R.periodic[a]) {
+                    if (c0 < 0) { cs[a][0] = 0; cs[a][1] = 1; cs[a][2] = nc - 1; }
+                    else if (c2 >= nc) { cs[a][0] = 0; cs[a][1] = nc - 2; cs[a][2] = nc - 1; }
+                    else { cs[a][0] = c0; cs[a][1] = ci[a]; cs[a][2] = c2; }
+                    ncs[a] = 3;
+                } else {
+                    if (c0 >= 0) cs[a][ncs[a]++] = c0;
+                    cs[a][ncs[a]++] = ci[a];
+                    if (c2 < nc) cs[a][ncs[a]++] = c2;
+                }
+            }
+        }
+        const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
+        int n = 0;
+        // cells in ascending order (x fastest), lanes over one cell's list at a time
+        for (int iz = 0; iz < ncs[2]; ++iz)
+            for (int iy = 0; iy < ncs[1]; ++iy)
+                for (int ix = 0; ix < ncs[0]; ++ix) {
+                    const int cell = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
+                    const int cnt = min(D.cell_cnt[cell], D.cell_cap);
+                    const int *ca = D.cell_atoms + (size_t)cell * D.cell_cap;
+                    for (int base = 0; base < cnt; base += 32) {
+                        const int c = base + lane;
+                        bool in = false;
+                        int j = -1;
+                        if (c < cnt) {
+                            j = ca[c];
+                            if (j != i) {
+                                const int4 pj = D.rec[j].p;
+                                const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
+                                const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
+                                const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
+                                const float r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 < D.rl2_lo_f) in = true;
+                                else if (r2 >= D.rl2_hi_f) in = false;
+                                else in = exact_r2(R, xi, D.x[j]) < D.rl2;
+                            }
                         }
-                        row[q] = j;
-                        ++cnt;
-                    } else {
-                        over = true;
+                        const unsigned m = __ballot_sync(full, in);
+                        if (in) {
+                            const int pos = n + __popc(m & ((1u << lane) - 1u));
+                            if (pos < cap) D.nbr[(size_t)pos * D.natom + i] = j;
+                        }
+                        n += __popc(m);
                     }
                 }
-            }
-    for (int k = 0; k < cnt; ++k) D.nbr[(size_t)k * D.natom + i] = row[k];
-    D.nnb[i] = cnt;
-    if (over) set_err(D, HD_ERR_OVERFLOW, i, r);
+        if (lane == 0) {
+            D.nnb[i] = min(n, cap);
+            if (n > cap) set_err(D, HD_ERR_OVERFLOW, i, r);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- pair sweep
@@ -315,7 +402,6 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     const float h0 = R.shiftf[ti][0], h1 = R.shiftf[ti][1];
     const float q0h = R.r0sq_hi[ti][0], q1h = R.r0sq_hi[ti][1];
     const float q0l = R.r0sq_lo[ti][0], q1l = R.r0sq_lo[ti][1];
-    const float rc2 = D.rc2f;
     const bool exact = R.exact_r2 != 0;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
     const int nn = act ? D.nnb[i] : 0;
@@ -324,6 +410,33 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     // software pipeline: the next neighbour's record is in flight while this one is used
     int jn = nn > 0 ? __ldg(nb) : i;
     AtomRec an = D.rec[jn];
+    // one pair's contribution (cancellation-free LJ form, exact r^2 when the
+    // replica's axes share one fixed-point unit)
+    auto term = [&](const AtomRec &aj, int ix, int iy, int iz, float dx, float dy, float dz, float r2) {
+        const int tj = aj.p.w & 1;
+        const float eps = tj ? e1 : e0;
+        float r2h = r2, r2l = 0.f;
+        if (exact) r2_split(R, ix, iy, iz, r2h, r2l);
+        const float ir2 = rcp_approx(r2h);
+        const float tt = (((tj ? q1h : q0h) - r2h) + ((tj ? q1l : q0l) - r2l)) * ir2;
+        const float u = 1.f + tt;
+        const float s6 = 0.5f * u * u * u;
+        const float w = tt * fmaf(tt, tt + 3.f, 3.f);          // 2 s^6 - 1
+        const float fr = 24.f * eps * ir2 * s6 * w;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
+        e = fmaf(0.5f, fmaf(4.f * eps * s6, s6 - 1.f, -(tj ? h1 : h0)), e);
+        if (!Q) {
+            const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
+            const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+            const float B = 96.f * eps * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
+            hx += fmaf(B, dx, -fr * ux);
+            hy += fmaf(B, dy, -fr * uy);
+            hz += fmaf(B, dz, -fr * uz);
+        }
+    };
+    bool band = false;
     for (int k = 0; k < nn; ++k) {
         const AtomRec aj = an;
         if (k + 1 < nn) {
@@ -336,28 +449,23 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
         const int iz = (int)((unsigned)pi.z - (unsigned)pj.z);
         const float dx = (float)ix * lx, dy = (float)iy * ly, dz = (float)iz * lz;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < rc2) {
-            const int tj = pj.w & 1;
-            const float eps = tj ? e1 : e0;
-            const float ir2 = rcp_approx(r2);
-            const float r2lo = exact ? r2_residual(R, ix, iy, iz, r2) : 0.f;
-            const float tt = (((tj ? q1h : q0h) - r2) + ((tj ? q1l : q0l) - r2lo)) * ir2;
-            const float u = 1.f + tt;
-            const float s6 = 0.5f * u * u * u;
-            const float w = tt * fmaf(tt, tt + 3.f, 3.f);          // 2 s^6 - 1
-            const float fr = 24.f * eps * ir2 * s6 * w;
-            fx = fmaf(fr, dx, fx);
-            fy = fmaf(fr, dy, fy);
-            fz = fmaf(fr, dz, fz);
-            e = fmaf(0.5f, fmaf(4.f * eps * s6, s6 - 1.f, -(tj ? h1 : h0)), e);
-            if (!Q) {
-                const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
-                const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-                const float B = 96.f * eps * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
-                hx += fmaf(B, dx, -fr * ux);
-                hy += fmaf(B, dy, -fr * uy);
-                hz += fmaf(B, dz, -fr * uz);
-            }
+        if (r2 < D.rc2_lo_f) term(aj, ix, iy, iz, dx, dy, dz, r2);
+        else band |= r2 < D.rc2_hi_f;
+    }
+    // Rare: pairs in a thin band around rc are cut by the oracle's FP64 test
+    // (same operations), so no pair is cut at a different step than in FP64.
+    if (band) {
+        const dbl4 xi64 = D.x[i];
+        for (int k = 0; k < nn; ++k) {
+            const int j = __ldg(nb + (size_t)k * stride);
+            const AtomRec aj = D.rec[j];
+            const int ix = (int)((unsigned)pi.x - (unsigned)aj.p.x);
+            const int iy = (int)((unsigned)pi.y - (unsigned)aj.p.y);
+            const int iz = (int)((unsigned)pi.z - (unsigned)aj.p.z);
+            const float dx = (float)ix * lx, dy = (float)iy * ly, dz = (float)iz * lz;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 >= D.rc2_lo_f && r2 < D.rc2_hi_f && exact_r2(R, xi64, D.x[j]) < D.rc2)
+                term(aj, ix, iy, iz, dx, dy, dz, r2);
         }
     }
     // undo the FP32 rounding of the per-axis fixed-point unit (uniform per axis)
@@ -375,36 +483,45 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     }
     const bool rig = role == ROLE_RIGID;
     const bool anyrig = __any_sync(0xffffffffu, rig);
+    // FP32 sums inside each warp, FP64 across warps and tiles
     if (!Q) {
-        double v[NPART] = {};
+        float v[12] = {};
         if (act) {
-            v[PART_D2] = (double)(dri.x * dri.x + dri.y * dri.y + dri.z * dri.z);
-            v[PART_G] = (double)(-(fx * dri.x + fy * dri.y + fz * dri.z));
-            v[PART_V] = (double)e;
+            v[PART_D2] = dri.x * dri.x + dri.y * dri.y + dri.z * dri.z;
+            v[PART_G] = -(fx * dri.x + fy * dri.y + fz * dri.z);
+            v[PART_V] = e;
         }
-        if (anyrig && rig) {
-            const dbl4 xi = D.x[i];
+        if (rig) {
             v[PART_FRIG] = fx; v[PART_FRIG + 1] = fy; v[PART_FRIG + 2] = fz;
             v[PART_HRIG] = hx; v[PART_HRIG + 1] = hy; v[PART_HRIG + 2] = hz;
             v[PART_DRRIG] = dri.x; v[PART_DRRIG + 1] = dri.y; v[PART_DRRIG + 2] = dri.z;
-            v[PART_XRIG] = xi.x; v[PART_XRIG + 1] = xi.y; v[PART_XRIG + 2] = xi.z;
         }
-        cta_reduce<NPART>(v, D.part + (size_t)t * NPART, -1);
-    } else {
-        double v[QPART] = {};
-        if (role == ROLE_MOBILE) {
-            const float4 vv = D.v32[i];
-            v[QP_FMAX2] = (double)fx * fx + (double)fy * fy + (double)fz * fz;
-            v[QP_P] = (double)(fx * vv.x + fy * vv.y + fz * vv.z);
-            v[QP_VV] = (double)(vv.x * vv.x + vv.y * vv.y + vv.z * vv.z);
-            v[QP_FF] = v[QP_FMAX2];
-        }
+        double xr[3] = {0.0, 0.0, 0.0};
         if (rig) {
             const dbl4 xi = D.x[i];
-            v[QP_FRIG] = fx; v[QP_FRIG + 1] = fy; v[QP_FRIG + 2] = fz;
-            v[QP_XRIG] = xi.x; v[QP_XRIG + 1] = xi.y; v[QP_XRIG + 2] = xi.z;
+            xr[0] = xi.x; xr[1] = xi.y; xr[2] = xi.z;
         }
-        cta_reduce<QPART>(v, D.part + (size_t)t * NPART, QP_FMAX2);
+        tile_reduce_mixed(v, anyrig ? 12 : 3, xr, anyrig, D.part + (size_t)t * NPART);
+    } else {
+        float v[12] = {};
+        float fm = 0.f;
+        if (role == ROLE_MOBILE) {
+            const float4 vv = D.v32[i];
+            fm = fx * fx + fy * fy + fz * fz;
+            v[QP_P] = fx * vv.x + fy * vv.y + fz * vv.z;
+            v[QP_VV] = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
+            v[QP_FF] = fm;
+        }
+        if (rig) {
+            v[QP_FRIG] = fx; v[QP_FRIG + 1] = fy; v[QP_FRIG + 2] = fz;
+        }
+        double xr[3] = {0.0, 0.0, 0.0};
+        if (rig) {
+            const dbl4 xi = D.x[i];
+            xr[0] = xi.x; xr[1] = xi.y; xr[2] = xi.z;
+        }
+        v[QP_FMAX2] = fm;
+        tile_reduce_quench(v, xr, anyrig, D.part + (size_t)t * NPART);
     }
 }
 
@@ -601,63 +718,64 @@ __global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
 }
 
 __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
+    // split form: FP32 forces, FP64 velocities and positions
     const int t = blockIdx.x, r = D.tile_rep[t];
     const RepDev &R = D.rep[r];
     const Scal &C = D.sc[r];
     const bool act = threadIdx.x < D.tile_n[t];
     const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
-    const int4 p = D.rec[i].p;
+    const AtomRec ai = D.rec[i];
+    const int4 p = ai.p;
     const int role = act ? ((p.w >> 8) & 0xff) : ROLE_FIXED;
     float kin = 0.f;
     if (role != ROLE_FIXED) {
-        const float hh = (float)(0.5 * D.dt);
-        float4 v = D.v32[i];
+        const double hh = 0.5 * D.dt;
+        dbl4 v = D.v64[i];
         dbl4 x = D.x[i];
         if (role == ROLE_MOBILE) {
-            const float4 F = D.f32[i], H = D.h32[i], dr = D.rec[i].d;
+            const float4 F = D.f32[i], H = D.h32[i], dr = ai.d;
             const float ca = (float)C.ca, cb = (float)C.cb;
-            const float Fx = fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
-            const float Fy = fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
-            const float Fz = fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
+            const double Fx = (double)fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
+            const double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
+            const double Fz = (double)fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
             const bool three = R.dim == 3;
-            if (mode & MODE_KIN) kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+            if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             if (mode & MODE_CLOSE) {
-                v.x = fmaf(hh, Fx, v.x);
-                v.y = fmaf(hh, Fy, v.y);
-                if (three) v.z = fmaf(hh, Fz, v.z);
-                kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+                v.x += hh * Fx;
+                v.y += hh * Fy;
+                if (three) v.z += hh * Fz;
+                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             }
             if (mode & MODE_OPEN) {
-                v.x = fmaf(hh, Fx, v.x);
-                v.y = fmaf(hh, Fy, v.y);
-                if (three) v.z = fmaf(hh, Fz, v.z);
-                const float ax = v.x, ay = v.y, az = v.z;
+                v.x += hh * Fx;
+                v.y += hh * Fy;
+                if (three) v.z += hh * Fz;
+                const double ax = v.x, ay = v.y, az = v.z;
                 float n0, n1, n2, n3;
                 normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
-                v.x = fmaf(R.c_ouf, v.x, R.s_ouf * n0);
-                v.y = fmaf(R.c_ouf, v.y, R.s_ouf * n1);
+                v.x = R.c_ou * v.x + R.s_ou * (double)n0;
+                v.y = R.c_ou * v.y + R.s_ou * (double)n1;
                 if (three) {
                     normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
-                    v.z = fmaf(R.c_ouf, v.z, R.s_ouf * n2);
+                    v.z = R.c_ou * v.z + R.s_ou * (double)n2;
                 }
-                x.x += (double)(hh * (ax + v.x));
-                x.y += (double)(hh * (ay + v.y));
-                if (three) x.z += (double)(hh * (az + v.z));
+                x.x += hh * (ax + v.x);
+                x.y += hh * (ay + v.y);
+                if (three) x.z += hh * (az + v.z);
             }
         } else {
-            if (mode & MODE_CLOSE) v = make_float4((float)C.vb_mid[0], (float)C.vb_mid[1], (float)C.vb_mid[2], 0.f);
+            if (mode & MODE_CLOSE) v = make_dbl4(C.vb_mid[0], C.vb_mid[1], C.vb_mid[2], 0.0);
             if (mode & MODE_OPEN) {
-                const double h = D.dt;
-                x.x += 0.5 * h * C.vb_new[0];
-                x.y += 0.5 * h * C.vb_new[1];
-                x.z += 0.5 * h * C.vb_new[2];
-                x.x += 0.5 * h * C.vb_new[0];
-                x.y += 0.5 * h * C.vb_new[1];
-                x.z += 0.5 * h * C.vb_new[2];
-                v = make_float4((float)C.vb_new[0], (float)C.vb_new[1], (float)C.vb_new[2], 0.f);
+                x.x += hh * C.vb_new[0];
+                x.y += hh * C.vb_new[1];
+                x.z += hh * C.vb_new[2];
+                x.x += hh * C.vb_new[0];
+                x.y += hh * C.vb_new[1];
+                x.z += hh * C.vb_new[2];
+                v = make_dbl4(C.vb_new[0], C.vb_new[1], C.vb_new[2], 0.0);
             }
         }
-        D.v32[i] = v;
+        D.v64[i] = v;
         if (mode & MODE_OPEN) {
             D.x[i] = x;
             const dbl4 xo = D.xo[i];
@@ -666,7 +784,8 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
         }
     }
     if (mode & (MODE_CLOSE | MODE_KIN)) {
-        double v1[1] = {(double)kin};
+        double v1[1] = {(double)warp_sum(kin)};
+        if ((threadIdx.x & 31) != 0) v1[0] = 0.0;
         cta_reduce<1>(v1, D.kpart + t, -1);
     }
 }
@@ -703,6 +822,9 @@ __global__ void k_qscalar(Dev D, int max_iter) {
     const RepDev &R = D.rep[r];
     RepState &S = D.st[r];
     Scal &C = D.sc[r];
+    // this iteration's list rebuild (if any) has been used by the pair pass
+    __syncthreads();
+    if (threadIdx.x == 0) D.rebuild[r] = 0;
     if (S.q_done) return;
     __shared__ double acc[QPART];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -886,7 +1008,8 @@ void launch_rebuild(const Dev &D, cudaStream_t s) {
     k_cell_clear<<<D.nrep, 256, 0, s>>>(D);
     k_bin<<<D.ntile, nthr(D), 0, s>>>(D);
     k_cellsort<<<dim3((D.max_cells + 127) / 128, D.nrep), 128, 0, s>>>(D);
-    k_nlist<<<D.ntile, nthr(D), 0, s>>>(D);
+    k_rebuild_plan<<<1, 32, 0, s>>>(D);
+    k_nlist<<<D.nl_grid, 256, 0, s>>>(D);
 }
 void launch_pair(const Dev &D, bool quench, cudaStream_t s) {
     if (D.prec == HD_FP64) {

@@ -339,10 +339,17 @@ def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_stat
         ob = b.obs(k)
         assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12)
     b.step(100)
+    report = []
     for k, o in enumerate(ors):
         o.run(100)
         ob = b.obs(k)
-        assert ob["t_h"] == pytest.approx(o.s.t_h, rel=1e-6)
-        assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12)
-        assert ob["sigma"] == pytest.approx(o.s.sigma, rel=1e-6)
+        report.append("replica %d (dim %d): rel err t_h %.2e, dV %.2e, sigma %.2e" % (
+            k, workload_states[k].dim, abs(ob["t_h"] / o.s.t_h - 1), abs(ob["dV"] / o.s.dV - 1),
+            abs(ob["sigma"] / o.s.sigma - 1)))
+    print("\n".join(report))
+    for k, o in enumerate(ors):
+        ob = b.obs(k)
+        assert ob["t_h"] == pytest.approx(o.s.t_h, rel=1e-6), report
+        assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12), report
+        assert ob["sigma"] == pytest.approx(o.s.sigma, rel=1e-6), report
     b.close()
