@@ -207,6 +207,25 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ main arm
+def committed_traffic(split):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    if not split:
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", "k_pair32_afm3d_hyper64.md")).read()
+        kv = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(("traffic_bytes", "kernel_sources")))
+        h = hashlib.sha256()
+        for f in ("hd_kernels.cu", "hd_internal.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_0909_5215_gb300", "csrc", f), "rb").read())
+        if h.hexdigest()[:16] != kv["kernel_sources_sha256_16"].strip():
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def mean_nnb(b):
     tot, cnt = 0, 0
     for r in range(b.n_rep):
@@ -307,7 +326,7 @@ def run_ours(args):
     nnb = mean_nnb(b)
     pair_ms = tim["pair_ms"] / max(1, tim["pair_launches"])
     bytes_per_atom = 4.0 * nnb + 4 + 16 + 16 + 16 + 16 + 32 if split else 4.0 * nnb + 4 + 32 + 32 + 32 + 32 + 64
-    traffic = None
+    traffic = committed_traffic(split)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -473,8 +473,11 @@ void set_scalars(Dev &D, const hd_params *p) {
     D.rc2f = (float)D.rc2;
     D.rl2_lo_f = (float)(D.rl2 * (1.0 - 1.0 / 4096.0));
     D.rl2_hi_f = (float)(D.rl2 * (1.0 + 1.0 / 4096.0));
-    D.rc2_lo_f = (float)(D.rc2 * (1.0 - 1.0 / 4096.0));
-    D.rc2_hi_f = (float)(D.rc2 * (1.0 + 1.0 / 4096.0));
+    // FP32 r^2 of the split sweep is within ~3e-7 (relative) of the oracle's
+    // FP64 r^2 (fixed-point rounding of positions plus FP32 rounding); the
+    // band decided in FP64 is 2^-20 ~ 9.5e-7 wide on each side
+    D.rc2_lo_f = (float)(D.rc2 * (1.0 - 1.0 / 1048576.0));
+    D.rc2_hi_f = (float)(D.rc2 * (1.0 + 1.0 / 1048576.0));
     D.half_skin2_f = (float)(D.half_skin2 * (1.0 - 1e-4));
     D.seed_lo = (uint32_t)p->seed;
     D.seed_hi = (uint32_t)(p->seed >> 32);

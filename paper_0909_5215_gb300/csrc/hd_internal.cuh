@@ -104,7 +104,7 @@ struct Dev {
     int q_method, max_cells;        // max_cells: largest cell count of one replica
     double dt, rc2, rl2, half_skin2, q_ftol, q_step, q_theta;
     float rc2f, rl2_lo_f, rl2_hi_f, half_skin2_f;
-    float rc2_lo_f, rc2_hi_f;    // rc^2 (1 -+ 2^-12): band decided in FP64
+    float rc2_lo_f, rc2_hi_f;    // rc^2 (1 -+ 2^-20): band decided in FP64
     uint32_t seed_lo, seed_hi;
     const RepDev *rep;
     RepState *st;
