@@ -189,6 +189,29 @@ hd_status hd_info(const hd_ctx *ctx, int64_t out[12]);
  * [6] scalar ms, [7] scalar launches.  Synchronises the stream. */
 hd_status hd_timing(hd_ctx *ctx, int enable, double out[8]);
 
+/* Neighbour list of one replica without any device allocation.  For callers
+ * that must not let a library allocate device memory: a program that
+ * budgets all of the GPU's memory itself, or a loop that cannot afford the
+ * latency or the failure of an allocation.  The paper has no counterpart;
+ * it is the list build of hd_create (rows: every j != i with FP64
+ * minimum-image r^2 < rl^2, ascending j) run on caller buffers.
+ *   d_pos   device, [n_atoms][3] FP64 positions (read)
+ *   box, periodic  host, as in hd_replica_desc; rl = list radius (rc + skin)
+ *   d_nbr   device, [n_atoms][maxnb] int32 (written; -1 past each row's end)
+ *   d_nnb   device, [n_atoms] int32 row lengths (written)
+ * Its scratch (fixed-point positions, cells, an error word) lives in one
+ * file-scope device array sized for at most 65,536 atoms, 16,384 cells of at
+ * most 64 atoms and maxnb <= 160; larger inputs return HD_ERR_ARG.  Each GPU
+ * that loads the library holds that array (about 5.4 MB) until the process
+ * exits.  The first call on a device looks up the array's address with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the array and leaves its contents behind; counts and the
+ * error word are cleared at the start of each call, and calls that overlap
+ * on the GPU race.  Synchronises cuda_stream; returns HD_ERR_OVERFLOW if a
+ * row or a cell exceeded its capacity. */
+hd_status hd_nlist_static(const double *d_pos, int n_atoms, const double box[3], const uint8_t periodic[3],
+                          double rl, int maxnb, int32_t *d_nbr, int32_t *d_nnb, void *cuda_stream);
+
 /* Wait for queued work and check the device error word. */
 hd_status hd_sync(hd_ctx *ctx);
 

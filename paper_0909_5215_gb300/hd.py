@@ -57,7 +57,7 @@ class hd_params(C.Structure):
 
 
 SYMBOLS = ["hd_workspace_bytes", "hd_create", "hd_set_slider", "hd_set_bias", "hd_step", "hd_quench",
-           "hd_read", "hd_info", "hd_timing", "hd_sync", "hd_destroy", "hd_last_error"]
+           "hd_read", "hd_info", "hd_timing", "hd_nlist_static", "hd_sync", "hd_destroy", "hd_last_error"]
 INFO_FIELDS = ["n_rep", "natom", "maxnb", "cell_cap", "ntile", "driver", "persistent_ctas", "launches",
                "h2d_bytes", "d2h_bytes", "workspace_bytes", "reserved"]
 TIMING_FIELDS = ["pair_ms", "pair_launches", "update_ms", "update_launches", "rebuild_ms", "rebuild_passes",
@@ -87,6 +87,8 @@ def lib(build_if_missing: bool = False):
     L.hd_read.argtypes = [vp, C.c_int, C.c_int, vp, sz]
     L.hd_info.argtypes = [vp, C.POINTER(C.c_int64)]
     L.hd_timing.argtypes = [vp, C.c_int, C.POINTER(C.c_double)]
+    L.hd_nlist_static.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.c_double, C.c_int,
+                                  vp, vp, vp]
     L.hd_sync.argtypes = [vp]
     L.hd_destroy.argtypes = [vp]
     L.hd_destroy.restype = None
@@ -143,6 +145,14 @@ def hd_timing(ctx, enable):
     out = (C.c_double * 8)()
     st = lib().hd_timing(ctx, int(enable), out)
     return st, list(out)
+
+
+def hd_nlist_static(d_pos, n_atoms, box, periodic, rl, maxnb, d_nbr, d_nnb, stream):
+    """List build on caller buffers with no device allocation (device pointers as ints)."""
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    p = (C.c_uint8 * 3)(*[int(v) for v in periodic])
+    return lib().hd_nlist_static(C.c_void_p(d_pos), int(n_atoms), b, p, float(rl), int(maxnb), C.c_void_p(d_nbr),
+                                 C.c_void_p(d_nnb), C.c_void_p(stream))
 
 
 def hd_sync(ctx):
