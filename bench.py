@@ -57,6 +57,19 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_over_ranks(seconds, work, dist=None, device=None):
+    """Whole-job timing across ranks: the slowest rank's time and the sum of
+    the work units (atom-steps, boosted time) of all ranks."""
+    if dist is None:
+        return float(seconds), [float(w) for w in work]
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(x) for x in work], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t.item()), [float(x) for x in w.tolist()]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -131,9 +144,15 @@ def build_workload(name, prec, rank):
 
 
 def prepare_batch(reps, params, driver, block, split, setup_md=1000):
-    from paper_0909_5215_gb300 import hd
-    drv = {"auto": hd.HD_DRIVER_AUTO, "kernels": hd.HD_DRIVER_KERNELS, "persistent": hd.HD_DRIVER_PERSISTENT}[driver]
+    from paper_0909_5215_gb300 import autotune, hd
+    tuned = None
+    if driver == "auto":
+        drv, block, ms = autotune.tune(reps, params)
+        tuned = {"driver": drv, "block": block, "ms_per_step": ms}
+    else:
+        drv = {"kernels": hd.HD_DRIVER_KERNELS, "persistent": hd.HD_DRIVER_PERSISTENT}[driver]
     b = hd.Batch(reps, params, driver=drv, block=block)
+    b.tuned = tuned
     # seed r_O with the quenched lattice, equilibrate, calibrate the bias band
     b.quench(method=1, ftol=1e-4 if split else 1e-6, max_iter=5000, theta=1e30, adopt=2)
     if setup_md > 0:
@@ -207,6 +226,22 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ main arm
+def kernel_code_hash():
+    """sha256 (16 hex digits) of the pair kernel's sources with comments and
+    blank lines removed: a capture stays valid across comment edits."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in ("hd_kernels.cu", "hd_internal.cuh"):
+        text = open(os.path.join(ROOT, "paper_0909_5215_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for line in text.splitlines():
+            line = re.sub(r"//.*", "", line).strip()
+            if line:
+                h.update(line.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
 def committed_traffic(split):
     """DRAM bytes per launch of the pair kernel from the committed ncu summary,
     or None when the kernel sources changed since that capture."""
@@ -215,11 +250,8 @@ def committed_traffic(split):
         return None
     try:
         text = open(os.path.join(ROOT, "profiles", "k_pair32_afm3d_hyper64.md")).read()
-        kv = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(("traffic_bytes", "kernel_sources")))
-        h = hashlib.sha256()
-        for f in ("hd_kernels.cu", "hd_internal.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_0909_5215_gb300", "csrc", f), "rb").read())
-        if h.hexdigest()[:16] != kv["kernel_sources_sha256_16"].strip():
+        kv = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith(("traffic_bytes", "kernel_code")))
+        if kernel_code_hash() != kv["kernel_code_sha256_16"].strip():
             return None
         return float(kv["traffic_bytes_per_launch"])
     except Exception:
@@ -289,19 +321,13 @@ def run_ours(args):
     info1 = b.info()
     ob1 = b.obs()
     th1 = ob1[:, 2]
-    sec = ms / 1000.0
+    atom_steps = natoms * args.md_steps * args.steps
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([sec], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-        h = torch.tensor([float((th1 - th0).sum())], device=dev, dtype=torch.float64)
-        dist.all_reduce(h)
-        dth = float(h.item())
+        sec, (total_steps, dth) = reduce_over_ranks(ms / 1000.0, [atom_steps, float((th1 - th0).sum())], dist, dev)
     else:
-        dth = float((th1 - th0).sum())
-    atom_steps = natoms * args.md_steps * args.steps
-    value = atom_steps * world / sec
+        sec, (total_steps, dth) = reduce_over_ranks(ms / 1000.0, [atom_steps, float((th1 - th0).sum())])
+    value = total_steps / sec
     launches = int(info1["launches"] - info0["launches"])
 
     # ---- end to end through the C ABI with host buffers
@@ -324,7 +350,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (pair sweep), events in the timed region
     nnb = mean_nnb(b)
-    pair_ms = tim["pair_ms"] / max(1, tim["pair_launches"])
+    pair_ms = tim["pair_ms"] / tim["pair_launches"] if tim["pair_launches"] else None
     bytes_per_atom = 4.0 * nnb + 4 + 16 + 16 + 16 + 16 + 32 if split else 4.0 * nnb + 4 + 32 + 32 + 32 + 32 + 64
     traffic = committed_traffic(split)
     peaks = {}
@@ -333,11 +359,17 @@ def run_ours(args):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_per_atom * natoms / (pair_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": "k_pair32<false>" if split else "k_pair64<false>",
-            "algorithmic_bytes_per_atom": bytes_per_atom, "mean_neighbours": nnb,
-            "pair_ms_per_launch": pair_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+    if pair_ms:
+        achieved = bytes_per_atom * natoms / (pair_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": "k_pair32<false>" if split else "k_pair64<false>",
+                "algorithmic_bytes_per_atom": bytes_per_atom, "mean_neighbours": nnb,
+                "pair_ms_per_launch": pair_ms,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    else:
+        # the persistent launch has no separate pair kernel to time
+        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
+                "kernel": "k_persist (phases fused; no per-phase timing)", "mean_neighbours": nnb}
     phases = {k: tim[k] for k in tim}
 
     # ---- FP64 form on the same workload (the plain path the split form is compared with)
@@ -379,6 +411,9 @@ def run_ours(args):
             "config": {"workload": args.workload, "replicas": len(reps), "atoms": natoms,
                        "md_steps_per_step": args.md_steps, "quench": "FIRE ftol %g, <= %d iters, theta 0.5" % (
                            args.quench_ftol, args.quench_iters),
+                       "driver": {1: "kernels", 2: "persistent"}.get(b.info()["driver"], "kernels"),
+                       "block": (b.tuned or {}).get("block") or args.block or 128,
+                       "autotune": b.tuned,
                        "precision": "split: FP32 pair/bias arithmetic, FP64 positions, sums, clocks" if split
                        else "FP64 throughout", "l2": "inputs larger than L2 (%.0f MB workspace)" % (
                            b.ws_bytes / 1e6), "parallelism": "replicas" if world == 1 else "replicas x%d ranks" % world},

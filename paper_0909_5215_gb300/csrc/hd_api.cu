@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -35,6 +36,7 @@ struct Plan {
     size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
     size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff;
+    size_t o_ctarep, o_pgfirst, o_pgcount;
 };
 
 size_t take(size_t &cur, size_t bytes) {
@@ -268,6 +270,9 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_adopt = take(cur, R * 4);
     P.o_orig = take(cur, N * 4);
     P.o_rboff = take(cur, (R + 1) * 4);
+    P.o_ctarep = take(cur, T * 4);       // at most one CTA per tile
+    P.o_pgfirst = take(cur, R * 4);
+    P.o_pgcount = take(cur, R * 4);
     P.bytes = (cur + ALIGN - 1) / ALIGN * ALIGN;
     return true;
 }
@@ -286,6 +291,7 @@ struct hd_ctx {
     long long launches = 0;
     std::map<int, cudaGraphExec_t> graphs;
     std::map<std::string, cudaGraphExec_t> qgraphs;
+    bool persist_graph_ok = true;
     std::vector<double> qdisp;
     std::vector<int> qflag;
     long long h2d = 0, d2h = 0;
@@ -437,6 +443,12 @@ void fill_dev(hd_ctx *c) {
     D.qdisp = at<unsigned long long>(b, P.o_qdisp);
     D.orig = at<int>(b, P.o_orig);
     D.rb_off = at<int>(b, P.o_rboff);
+    D.cta_rep = at<int>(b, P.o_ctarep);
+    // test hook for the barrier time-out path: HD_TEST_SKIP_ARRIVE=<replica>
+    D.fault_rep = -1;
+    if (const char *e = getenv("HD_TEST_SKIP_ARRIVE")) D.fault_rep = atoi(e);
+    D.pg_first = at<int>(b, P.o_pgfirst);
+    D.pg_count = at<int>(b, P.o_pgcount);
     D.nl_pow2 = 32;
     while (D.nl_pow2 < P.maxnb) D.nl_pow2 <<= 1;
     {
@@ -538,6 +550,58 @@ hd_status refresh_md(hd_ctx *c, bool relist) {
     return HD_OK;
 }
 
+// Persistent launch: CTAs per replica in proportion to its pair work (3-D
+// atoms have ~4x the neighbours of 2-D ones), at least one and at most one
+// per tile, all resident at once.  Returns false when the batch has more
+// replicas than resident CTAs.
+bool setup_persistent(hd_ctx *c) {
+    const Plan &P = c->P;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (P.block > 128) return false;  // the persistent kernel is built for tiles of <= 128 atoms
+    const int bps = persist_blocks_per_sm(P.prec, P.block);
+    const long long maxg = (long long)bps * nsm;
+    if (!coop || bps <= 0 || P.nrep > maxg) return false;
+    std::vector<double> w(P.nrep);
+    double wsum = 0.0;
+    for (int r = 0; r < P.nrep; ++r) {
+        w[r] = (double)P.rep[r].n * (P.rep[r].dim == 3 ? 1.0 : 0.25);
+        wsum += w[r];
+    }
+    std::vector<int> cnt(P.nrep);
+    long long tot = 0;
+    for (int r = 0; r < P.nrep; ++r) {
+        int k = (int)std::floor(w[r] / wsum * (double)maxg);
+        k = std::max(1, std::min(k, P.rep[r].ntile));
+        cnt[r] = k;
+        tot += k;
+    }
+    while (tot > maxg) {
+        int big = 0;
+        for (int r = 1; r < P.nrep; ++r)
+            if (cnt[r] > cnt[big]) big = r;
+        if (cnt[big] <= 1) return false;
+        --cnt[big];
+        --tot;
+    }
+    std::vector<int> first(P.nrep), ctarep;
+    for (int r = 0; r < P.nrep; ++r) {
+        first[r] = (int)ctarep.size();
+        for (int k = 0; k < cnt[r]; ++k) ctarep.push_back(r);
+    }
+    if (cudaMemcpyAsync((void *)c->D.cta_rep, ctarep.data(), ctarep.size() * 4, cudaMemcpyHostToDevice, c->s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync((void *)c->D.pg_first, first.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync((void *)c->D.pg_count, cnt.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s) != cudaSuccess)
+        return false;
+    c->persistent_ctas = (int)ctarep.size();
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -563,7 +627,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
         return fail(c, HD_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, c->P.bytes);
     c->ws = (char *)d_workspace;
     c->s = (cudaStream_t)cuda_stream;
-    c->driver = (p->driver == HD_DRIVER_PERSISTENT) ? HD_DRIVER_PERSISTENT : HD_DRIVER_KERNELS;
+    c->driver = HD_DRIVER_KERNELS;
     fill_dev(c);
     set_scalars(c->D, p);
     set_scalars(c->Q, p);
@@ -628,6 +692,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     CK(cudaGetLastError());
     c->qdisp.assign(P.nrep, 0.0);
     c->qflag.assign(P.nrep, 0);
+    if (p->driver == HD_DRIVER_PERSISTENT && setup_persistent(c)) c->driver = HD_DRIVER_PERSISTENT;
     return check_device(c);
 }
 
@@ -677,6 +742,37 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     CK(cudaStreamIsCapturing(c->s, &cs));
     const bool can_graph = c->s != nullptr && cs == cudaStreamCaptureStatusNone;
     if (c->timing && !c->graph_pending.empty()) harvest_all(c);
+    if (c->driver == HD_DRIVER_PERSISTENT) {
+        // one cooperative launch for all n steps, replayed from a graph when the
+        // runtime captures it; launched directly otherwise
+        if (can_graph && c->persist_graph_ok) {
+            auto it = c->graphs.find(n_steps);
+            if (it == c->graphs.end()) {
+                cudaGraph_t g = nullptr;
+                cudaGraphExec_t ge = nullptr;
+                bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                cudaError_t le = ok ? launch_persist(c->D, c->persistent_ctas, n_steps, c->s) : cudaErrorUnknown;
+                cudaError_t ee = ok ? cudaStreamEndCapture(c->s, &g) : cudaErrorUnknown;
+                ok = ok && le == cudaSuccess && ee == cudaSuccess && g &&
+                     cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+                (void)cudaGetLastError();
+                if (!ok) {
+                    c->persist_graph_ok = false;
+                } else {
+                    it = c->graphs.emplace(n_steps, ge).first;
+                }
+            }
+            if (c->persist_graph_ok) {
+                CK(cudaGraphLaunch(it->second, c->s));
+                c->launches += 1;
+                return HD_OK;
+            }
+        }
+        CK(launch_persist(c->D, c->persistent_ctas, n_steps, c->s));
+        c->launches += 1;
+        return HD_OK;
+    }
     if (!can_graph) {
         queue_steps(c, n_steps, &c->pending);
         CK(cudaGetLastError());

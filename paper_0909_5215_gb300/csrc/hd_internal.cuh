@@ -123,6 +123,9 @@ struct Dev {
     unsigned long long *qdisp;   // per replica max |x_q - r_O|^2 (bits of the double)
     const int *orig;             // per slot: index of the atom in its replica's input
     int *rb_off;                 // [nrep + 1] compacted atom offsets of rebuilding replicas
+    const int *cta_rep;          // persistent launch: replica of each CTA (-1: spare)
+    const int *pg_first, *pg_count;  // persistent launch: first CTA and CTA count of each replica
+    int fault_rep;               // test hook (-1 off): a CTA of this replica skips one barrier arrival
     int nl_pow2, nl_grid;        // neighbour-row buffer (power of two >= maxnb), k_nlist CTAs
 };
 

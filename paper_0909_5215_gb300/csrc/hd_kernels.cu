@@ -147,8 +147,8 @@ __global__ void k_cell_clear(Dev D) {
     for (int c = threadIdx.x; c < R.ncell; c += blockDim.x) D.cell_cnt[R.cell0 + c] = 0;
 }
 
-__global__ void k_bin(Dev D) {
-    const int t = blockIdx.x, r = D.tile_rep[t];
+__device__ __forceinline__ void dev_bin(const Dev &D, int t) {
+    const int r = D.tile_rep[t];
     if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
     const int i = D.tile_start[t] + threadIdx.x;
     const RepDev &R = D.rep[r];
@@ -161,16 +161,12 @@ __global__ void k_bin(Dev D) {
     else set_err(D, HD_ERR_OVERFLOW, i, r);
     D.pfixb[i] = p;
 }
+__global__ void k_bin(Dev D) { dev_bin(D, blockIdx.x); }
 
 // Each cell's atom list in ascending slot order (one thread per cell).  With
 // atoms stored cell-major, walking the neighbour cells in ascending cell
 // order then yields candidates in (almost) ascending j.
-__global__ void k_cellsort(Dev D) {
-    const int r = blockIdx.y;
-    if (!D.rebuild[r]) return;
-    const RepDev &R = D.rep[r];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= R.ncell) return;
+__device__ __forceinline__ void dev_cellsort_one(const Dev &D, const RepDev &R, int c) {
     int *a = D.cell_atoms + (size_t)(R.cell0 + c) * D.cell_cap;
     const int m = min(D.cell_cnt[R.cell0 + c], D.cell_cap);
     for (int k = 1; k < m; ++k) {
@@ -182,6 +178,13 @@ __global__ void k_cellsort(Dev D) {
         }
         a[q] = v;
     }
+}
+__global__ void k_cellsort(Dev D) {
+    const int r = blockIdx.y;
+    if (!D.rebuild[r]) return;
+    const RepDev &R = D.rep[r];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < R.ncell) dev_cellsort_one(D, R, c);
 }
 
 // Prefix of the atom counts of the replicas whose rebuild flag is set:
@@ -204,12 +207,80 @@ __global__ void k_rebuild_plan(Dev D) {
 // operation), and accepted j are packed in candidate order by ballot.  The
 // row order is thus a deterministic function of the cell lists (sorted by
 // k_cellsort); reads return each row ascending in j.
+__device__ __forceinline__ void dev_nlist_atom(const Dev &D, int r, int i, int lane) {
+    const unsigned full = 0xffffffffu;
+    const int cap = D.maxnb;
+    const RepDev &R = D.rep[r];
+    const int4 pi = D.rec[i].p;
+    const dbl4 xi = D.x[i];
+    const int cid = D.cellid[i];
+    const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
+    int cs[3][3], ncs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int nc = R.nc[a];
+        ncs[a] = 0;
+        if (nc == 1) {
+            cs[a][ncs[a]++] = 0;
+        } else {
+            // ascending: a periodic wrap puts nc-1 after 0 and 1
+            const int c0 = ci[a] - 1, c2 = ci[a] + 1;
+            if (R.periodic[a]) {
+                if (c0 < 0) { cs[a][0] = 0; cs[a][1] = 1; cs[a][2] = nc - 1; }
+                else if (c2 >= nc) { cs[a][0] = 0; cs[a][1] = nc - 2; cs[a][2] = nc - 1; }
+                else { cs[a][0] = c0; cs[a][1] = ci[a]; cs[a][2] = c2; }
+                ncs[a] = 3;
+            } else {
+                if (c0 >= 0) cs[a][ncs[a]++] = c0;
+                cs[a][ncs[a]++] = ci[a];
+                if (c2 < nc) cs[a][ncs[a]++] = c2;
+            }
+        }
+    }
+    const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
+    int n = 0;
+    // cells in ascending order (x fastest), lanes over one cell's list at a time
+    for (int iz = 0; iz < ncs[2]; ++iz)
+        for (int iy = 0; iy < ncs[1]; ++iy)
+            for (int ix = 0; ix < ncs[0]; ++ix) {
+                const int cell = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
+                const int cnt = min(D.cell_cnt[cell], D.cell_cap);
+                const int *ca = D.cell_atoms + (size_t)cell * D.cell_cap;
+                for (int base = 0; base < cnt; base += 32) {
+                    const int c = base + lane;
+                    bool in = false;
+                    int j = -1;
+                    if (c < cnt) {
+                        j = ca[c];
+                        if (j != i) {
+                            const int4 pj = D.rec[j].p;
+                            const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
+                            const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
+                            const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < D.rl2_lo_f) in = true;
+                            else if (r2 >= D.rl2_hi_f) in = false;
+                            else in = exact_r2(R, xi, D.x[j]) < D.rl2;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(full, in);
+                    if (in) {
+                        const int pos = n + __popc(m & ((1u << lane) - 1u));
+                        if (pos < cap) D.nbr[(size_t)pos * D.natom + i] = j;
+                    }
+                    n += __popc(m);
+                }
+            }
+    if (lane == 0) {
+        D.nnb[i] = min(n, cap);
+        if (n > cap) set_err(D, HD_ERR_OVERFLOW, i, r);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_nlist(Dev D) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned full = 0xffffffffu;
     const int total = D.rb_off[D.nrep];
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int cap = D.maxnb;
     for (int idx = blockIdx.x * (blockDim.x >> 5) + wib; idx < total; idx += nwarps) {
         int lo = 0, hi = D.nrep - 1;
         while (lo < hi) {
@@ -217,73 +288,7 @@ __global__ void __launch_bounds__(256) k_nlist(Dev D) {
             if (D.rb_off[mid] <= idx) lo = mid;
             else hi = mid - 1;
         }
-        const int r = lo;
-        const RepDev &R = D.rep[r];
-        const int i = R.atom0 + (idx - D.rb_off[r]);
-        const int4 pi = D.rec[i].p;
-        const dbl4 xi = D.x[i];
-        const int cid = D.cellid[i];
-        const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
-        int cs[3][3], ncs[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int nc = R.nc[a];
-            ncs[a] = 0;
-            if (nc == 1) {
-                cs[a][ncs[a]++] = 0;
-            } else {
-                // ascending: a periodic wrap puts nc-1 after 0 and 1
-                const int c0 = ci[a] - 1, c2 = ci[a] + 1;
-                if (R.periodic[a]) {
-                    if (c0 < 0) { cs[a][0] = 0; cs[a][1] = 1; cs[a][2] = nc - 1; }
-                    else if (c2 >= nc) { cs[a][0] = 0; cs[a][1] = nc - 2; cs[a][2] = nc - 1; }
-                    else { cs[a][0] = c0; cs[a][1] = ci[a]; cs[a][2] = c2; }
-                    ncs[a] = 3;
-                } else {
-                    if (c0 >= 0) cs[a][ncs[a]++] = c0;
-                    cs[a][ncs[a]++] = ci[a];
-                    if (c2 < nc) cs[a][ncs[a]++] = c2;
-                }
-            }
-        }
-        const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
-        int n = 0;
-        // cells in ascending order (x fastest), lanes over one cell's list at a time
-        for (int iz = 0; iz < ncs[2]; ++iz)
-            for (int iy = 0; iy < ncs[1]; ++iy)
-                for (int ix = 0; ix < ncs[0]; ++ix) {
-                    const int cell = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
-                    const int cnt = min(D.cell_cnt[cell], D.cell_cap);
-                    const int *ca = D.cell_atoms + (size_t)cell * D.cell_cap;
-                    for (int base = 0; base < cnt; base += 32) {
-                        const int c = base + lane;
-                        bool in = false;
-                        int j = -1;
-                        if (c < cnt) {
-                            j = ca[c];
-                            if (j != i) {
-                                const int4 pj = D.rec[j].p;
-                                const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
-                                const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
-                                const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
-                                const float r2 = dx * dx + dy * dy + dz * dz;
-                                if (r2 < D.rl2_lo_f) in = true;
-                                else if (r2 >= D.rl2_hi_f) in = false;
-                                else in = exact_r2(R, xi, D.x[j]) < D.rl2;
-                            }
-                        }
-                        const unsigned m = __ballot_sync(full, in);
-                        if (in) {
-                            const int pos = n + __popc(m & ((1u << lane) - 1u));
-                            if (pos < cap) D.nbr[(size_t)pos * D.natom + i] = j;
-                        }
-                        n += __popc(m);
-                    }
-                }
-        if (lane == 0) {
-            D.nnb[i] = min(n, cap);
-            if (n > cap) set_err(D, HD_ERR_OVERFLOW, i, r);
-        }
+        dev_nlist_atom(D, lo, D.rep[lo].atom0 + (idx - D.rb_off[lo]), lane);
     }
 }
 
@@ -294,8 +299,8 @@ __global__ void __launch_bounds__(256) k_nlist(Dev D) {
 //   -A = 24 eps s^6 (2 s^6 - 1)/r^2,   B = 96 eps s^6 (7 s^6 - 2)/r^4.
 // Q (quench): positions of the quench copy, no H.dr, quench partial sums.
 template <bool Q>
-__global__ void __launch_bounds__(256) k_pair64(Dev D) {
-    const int t = blockIdx.x, r = D.tile_rep[t];
+__device__ __forceinline__ void dev_pair64(const Dev &D, int t) {
+    const int r = D.tile_rep[t];
     if (Q && D.st[r].q_done) return;
     const RepDev &R = D.rep[r];
     const bool act = threadIdx.x < D.tile_n[t];
@@ -387,8 +392,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 template <bool Q>
-__global__ void __launch_bounds__(256) k_pair32(Dev D) {
-    const int t = blockIdx.x, r = D.tile_rep[t];
+__device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
+    const int r = D.tile_rep[t];
     if (Q && D.st[r].q_done) return;
     const RepDev &R = D.rep[r];
     const bool act = threadIdx.x < D.tile_n[t];
@@ -408,7 +413,8 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     const int *nb = D.nbr + i;
     const size_t stride = (size_t)D.natom;
     // software pipeline: the next neighbour's record is in flight while this one is used
-    int jn = nn > 0 ? __ldg(nb) : i;
+    // plain loads: in the persistent launch the list is rewritten between steps
+    int jn = nn > 0 ? nb[0] : i;
     AtomRec an = D.rec[jn];
     // one pair's contribution (cancellation-free LJ form, exact r^2 when the
     // replica's axes share one fixed-point unit)
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     for (int k = 0; k < nn; ++k) {
         const AtomRec aj = an;
         if (k + 1 < nn) {
-            jn = __ldg(nb + (size_t)(k + 1) * stride);
+            jn = nb[(size_t)(k + 1) * stride];
             an = D.rec[jn];
         }
         const int4 pj = aj.p;
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     if (band) {
         const dbl4 xi64 = D.x[i];
         for (int k = 0; k < nn; ++k) {
-            const int j = __ldg(nb + (size_t)k * stride);
+            const int j = nb[(size_t)k * stride];
             const AtomRec aj = D.rec[j];
             const int ix = (int)((unsigned)pi.x - (unsigned)aj.p.x);
             const int iy = (int)((unsigned)pi.y - (unsigned)aj.p.y);
@@ -525,6 +531,11 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
     }
 }
 
+template <bool Q>
+__global__ void __launch_bounds__(256) k_pair64(Dev D) { dev_pair64<Q>(D, blockIdx.x); }
+template <bool Q>
+__global__ void __launch_bounds__(256) k_pair32(Dev D) { dev_pair32<Q>(D, blockIdx.x); }
+
 // ---------------------------------------------------------------- per-replica scalars
 // Gathers the replica's tile sums (warp q sums slot q over the tiles in a
 // fixed order) and evaluates, in FP64:
@@ -535,10 +546,8 @@ __global__ void __launch_bounds__(256) k_pair32(Dev D) {
 //   cb = DeltaV' sigma / d^2 (from grad sigma = (H dr + g)/d - sigma dr/d^2);
 //   rigid-body force = sum_rigid F - gs - DeltaV' sum_rigid grad sigma;
 //   body kicks and the clocks: t_h += dt exp(DeltaV / kT) (Eq. 3).
-__device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, double ksum) {
+__device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, double ksum, RepState &S, Scal &C) {
     const RepDev &R = D.rep[r];
-    RepState &S = D.st[r];
-    Scal &C = D.sc[r];
     const int nr = R.nrig, dim = R.dim, vert = R.vert;
     double xT[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
     if (nr > 0) {
@@ -594,25 +603,38 @@ __device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, do
     for (int a = 0; a < 3; ++a) { C.vb_new[a] = vb[a]; S.vbody[a] = vb[a]; }
     S.K = ksum + 0.5 * (double)nr * (S.vbody_full[0] * S.vbody_full[0] + S.vbody_full[1] * S.vbody_full[1] +
                                      S.vbody_full[2] * S.vbody_full[2]);
-    if (D.rebuild[r]) {
-        if (D.rebuild[r] == 1) S.n_rebuild += 1;
-        D.rebuild[r] = 0;
+}
+
+// Tile sums of one replica, slot by slot (slot NPART = kinetic parts): for
+// each slot, lane l adds tiles l, l+32, ... in order, then a fixed warp
+// tree; the result does not depend on which warp of which CTA computes it.
+__device__ __forceinline__ void dev_scalar_acc(const Dev &D, int r, double *acc) {
+    const RepDev &R = D.rep[r];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = w; q <= NPART; q += nw) {
+        double a = 0.0;
+        for (int t = R.tile0 + lane; t < R.tile0 + R.ntile; t += 32)
+            a += (q < NPART) ? D.part[(size_t)t * NPART + q] : D.kpart[t];
+        a = warp_sum(a);
+        if (lane == 0) acc[q] = a;
     }
+    __syncthreads();
 }
 
 // blockDim = 32 * (NPART + 1): warp q < NPART sums partial slot q, warp NPART sums K.
 __global__ void k_scalar(Dev D, int mode) {
     const int r = blockIdx.x;
-    const RepDev &R = D.rep[r];
     __shared__ double acc[NPART + 1];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double a = 0.0;
-    for (int t = R.tile0 + lane; t < R.tile0 + R.ntile; t += 32)
-        a += (w < NPART) ? D.part[(size_t)t * NPART + w] : D.kpart[t];
-    a = warp_sum(a);
-    if (lane == 0) acc[w] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) scalar_eval(D, r, mode, acc, acc[NPART]);
+    dev_scalar_acc(D, r, acc);
+    if (threadIdx.x == 0) {
+        scalar_eval(D, r, mode, acc, acc[NPART], D.st[r], D.sc[r]);
+        // the list (if rebuilt this step) has been used; count displacement-triggered builds
+        const int f = D.rebuild[r];
+        if (f) {
+            if (f == 1) D.st[r].n_rebuild += 1;
+            D.rebuild[r] = 0;
+        }
+    }
 }
 
 // Kinetic energy of the last full step (observables only).
@@ -646,10 +668,9 @@ __device__ __forceinline__ void post_move(const Dev &D, const RepDev &R, int r, 
         set_err(D, HD_ERR_NUMERIC, i, r);
 }
 
-__global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
-    const int t = blockIdx.x, r = D.tile_rep[t];
+__device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, const Scal &C) {
+    const int r = D.tile_rep[t];
     const RepDev &R = D.rep[r];
-    const Scal &C = D.sc[r];
     const bool act = threadIdx.x < D.tile_n[t];
     const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
     const int4 p = D.rec[i].p;
@@ -717,11 +738,10 @@ __global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
+__device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, const Scal &C) {
     // split form: FP32 forces, FP64 velocities and positions
-    const int t = blockIdx.x, r = D.tile_rep[t];
+    const int r = D.tile_rep[t];
     const RepDev &R = D.rep[r];
-    const Scal &C = D.sc[r];
     const bool act = threadIdx.x < D.tile_n[t];
     const int i = D.tile_start[t] + (act ? threadIdx.x : 0);
     const AtomRec ai = D.rec[i];
@@ -788,6 +808,13 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
         if ((threadIdx.x & 31) != 0) v1[0] = 0.0;
         cta_reduce<1>(v1, D.kpart + t, -1);
     }
+}
+
+__global__ void __launch_bounds__(256) k_update64(Dev D, int mode) {
+    dev_update64(D, blockIdx.x, mode, D.sc[D.tile_rep[blockIdx.x]]);
+}
+__global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
+    dev_update32(D, blockIdx.x, mode, D.sc[D.tile_rep[blockIdx.x]]);
 }
 
 // ---------------------------------------------------------------- quench
@@ -998,6 +1025,122 @@ __global__ void k_adopt(Dev Q, Dev M, const int *adopt) {
     else M.rec[i].d = make_float4((float)(x.x - q.x), (float)(x.y - q.y), (float)(x.z - q.z), 0.f);
 }
 
+// ---------------------------------------------------------------- persistent driver
+// One launch steps every replica n times.  Replica r owns CTAs
+// [pg_first[r], pg_first[r] + pg_count[r]); each CTA takes the replica's
+// tiles round robin and runs the same per-tile phases as the per-phase
+// kernels; the compiler may contract multiply-adds differently where a phase
+// is inlined here, so the two drivers agree to rounding.  Phases of one
+// replica are separated by that replica's own barrier: a counter in global
+// memory (reset before each launch) that CTAs increment and poll.  Polling
+// is bounded: after ~2^24 polls the CTA records HD_ERR_TIMEOUT, raises the
+// abort word err[3], and every CTA leaves at its next barrier.  The launch
+// is cooperative, so all CTAs are resident.  A one-CTA replica uses only
+// __syncthreads().
+__device__ __forceinline__ bool grp_barrier(const Dev &D, int r, int nc, unsigned &epoch) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (nc > 1) {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            __threadfence();
+            const unsigned target = (epoch + 1u) * (unsigned)nc;
+            // test hook: one CTA of replica fault_rep skips its first arrival
+            const bool skip = D.fault_rep == r && epoch == 0 && blockIdx.x == (unsigned)D.pg_first[r];
+            if (!skip) atomicAdd(D.bar + r, 1u);
+            unsigned polls = 0;
+            while (*((volatile unsigned *)(D.bar + r)) < target) {
+                if (*((volatile int *)(D.err + 3)) != 0) { ok = 0; break; }
+                if (++polls > (1u << 24)) {
+                    set_err(D, HD_ERR_TIMEOUT, -1, r);
+                    atomicExch(D.err + 3, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return false;
+    }
+    ++epoch;
+    return true;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
+    const int r = D.cta_rep[blockIdx.x];
+    if (r < 0) return;
+    const RepDev &R = D.rep[r];
+    const int nc = D.pg_count[r], me = blockIdx.x - D.pg_first[r];
+    const bool leader = me == 0;
+    __shared__ RepState S;
+    __shared__ Scal C;
+    __shared__ double acc[NPART + 1];
+    __shared__ int s_flag;
+    if (threadIdx.x == 0) {
+        S = D.st[r];
+        C = D.sc[r];
+    }
+    __syncthreads();
+    unsigned epoch = 0;
+    auto scalars = [&](int mode) {
+        dev_scalar_acc(D, r, acc);
+        if (threadIdx.x == 0) {
+            scalar_eval(D, r, mode, acc, acc[NPART], S, C);
+            if (leader) {
+                D.st[r] = S;
+                D.sc[r] = C;
+            }
+        }
+        __syncthreads();
+    };
+    auto update = [&](int mode) {
+        for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc) {
+            if (PREC == HD_FP64) dev_update64(D, t, mode, C);
+            else dev_update32(D, t, mode, C);
+        }
+    };
+    // opening half of the first step, from the forces of the last call
+    scalars(MODE_OPEN);
+    update(MODE_OPEN);
+    if (!grp_barrier(D, r, nc, epoch)) return;
+    for (int k = 1; k <= nsteps; ++k) {
+        if (threadIdx.x == 0) s_flag = *((volatile int *)(D.rebuild + r));
+        __syncthreads();
+        const int flag = s_flag;
+        if (flag) {
+            for (int c = me * blockDim.x + threadIdx.x; c < R.ncell; c += nc * blockDim.x) D.cell_cnt[R.cell0 + c] = 0;
+            if (!grp_barrier(D, r, nc, epoch)) return;
+            for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc) dev_bin(D, t);
+            if (!grp_barrier(D, r, nc, epoch)) return;
+            for (int c = me * blockDim.x + threadIdx.x; c < R.ncell; c += nc * blockDim.x) dev_cellsort_one(D, R, c);
+            if (!grp_barrier(D, r, nc, epoch)) return;
+            // every CTA has read the flag before the first barrier above
+            if (threadIdx.x == 0) {
+                if (flag == 1) S.n_rebuild += 1;
+                if (leader) D.rebuild[r] = 0;
+            }
+            const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc)
+                for (int a = wib; a < D.tile_n[t]; a += nw) dev_nlist_atom(D, r, D.tile_start[t] + a, lane);
+            __syncthreads();
+        }
+        for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc) {
+            if (PREC == HD_FP64) dev_pair64<false>(D, t);
+            else dev_pair32<false>(D, t);
+        }
+        if (!grp_barrier(D, r, nc, epoch)) return;
+        const int mode = k < nsteps ? (MODE_CLOSE | MODE_OPEN) : MODE_CLOSE;
+        scalars(mode);
+        update(mode);
+        if (!grp_barrier(D, r, nc, epoch)) return;
+    }
+    if (leader && threadIdx.x == 0) D.st[r] = S;
+}
+
 // ---------------------------------------------------------------- launchers
 static inline int nthr(const Dev &D) { return D.block; }
 
@@ -1036,6 +1179,30 @@ void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s) {
     k_qupdate<<<Q.ntile, nthr(Q), 0, s>>>(Q);
 }
 void launch_qdisp(const Dev &Q, cudaStream_t s) { k_qdisp<<<Q.ntile, nthr(Q), 0, s>>>(Q); }
+int persist_blocks_per_sm(int prec, int block) {
+    int nb = 0;
+    if (prec == HD_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP64>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP32_SPLIT>, block, 0);
+    return nb;
+}
+cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(D.bar, 0, sizeof(unsigned) * D.nrep, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(D.err + 3, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(D.block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (D.prec == HD_FP64) return cudaLaunchKernelEx(&cfg, k_persist<HD_FP64>, D, nsteps);
+    return cudaLaunchKernelEx(&cfg, k_persist<HD_FP32_SPLIT>, D, nsteps);
+}
 void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s) {
     k_adopt<<<M.ntile, nthr(M), 0, s>>>(Q, M, adopt);
 }

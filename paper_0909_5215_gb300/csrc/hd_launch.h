@@ -17,5 +17,7 @@ void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s);
 void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 6 kernels
 void launch_qdisp(const Dev &Q, cudaStream_t s);
 void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s);
+int persist_blocks_per_sm(int prec, int block);                   // resident CTAs of the persistent kernel
+cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s);  // cooperative, n steps
 
 }  // namespace hd
