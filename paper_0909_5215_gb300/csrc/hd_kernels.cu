@@ -204,8 +204,12 @@ __global__ void k_rebuild_plan(Dev D) {
 // walked in ascending cell order, the lanes testing one cell's list at a time
 // (an FP32 test on the exact integer differences decides all but a thin band
 // around the radius, where the oracle's FP64 test is repeated operation for
-// operation), and accepted j are packed in candidate order by ballot.  The
-// row order is thus a deterministic function of the cell lists (sorted by
+// operation), and accepted j are packed by ballot: those within the cutoff rc
+// at build time from the front of the row in candidate order, the skin shell
+// from the back, and the shell block is then moved down behind the inner
+// one.  Lanes of the pair sweep thus cross from inside to outside rc at
+// nearly the same k, and whole warps skip the tail of their rows.  The row
+// order is a deterministic function of the cell lists (sorted by
 // k_cellsort); reads return each row ascending in j.
 __device__ __forceinline__ void dev_nlist_atom(const Dev &D, int r, int i, int lane) {
     const unsigned full = 0xffffffffu;
@@ -238,7 +242,8 @@ __device__ __forceinline__ void dev_nlist_atom(const Dev &D, int r, int i, int l
         }
     }
     const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
-    int n = 0;
+    const size_t stride = (size_t)D.natom;
+    int n_in = 0, n_sh = 0;
     // cells in ascending order (x fastest), lanes over one cell's list at a time
     for (int iz = 0; iz < ncs[2]; ++iz)
         for (int iy = 0; iy < ncs[1]; ++iy)
@@ -248,7 +253,7 @@ __device__ __forceinline__ void dev_nlist_atom(const Dev &D, int r, int i, int l
                 const int *ca = D.cell_atoms + (size_t)cell * D.cell_cap;
                 for (int base = 0; base < cnt; base += 32) {
                     const int c = base + lane;
-                    bool in = false;
+                    bool in = false, inner = false;
                     int j = -1;
                     if (c < cnt) {
                         j = ca[c];
@@ -261,23 +266,42 @@ __device__ __forceinline__ void dev_nlist_atom(const Dev &D, int r, int i, int l
                             if (r2 < D.rl2_lo_f) in = true;
                             else if (r2 >= D.rl2_hi_f) in = false;
                             else in = exact_r2(R, xi, D.x[j]) < D.rl2;
+                            inner = in && r2 < D.rc2_lo_f;
                         }
                     }
                     const unsigned m = __ballot_sync(full, in);
+                    const unsigned mi = __ballot_sync(full, inner);
                     if (in) {
-                        const int pos = n + __popc(m & ((1u << lane) - 1u));
-                        if (pos < cap) D.nbr[(size_t)pos * D.natom + i] = j;
+                        const unsigned below = (1u << lane) - 1u;
+                        const int pos = inner ? n_in + __popc(mi & below) : cap - 1 - (n_sh + __popc(m & ~mi & below));
+                        if (pos >= 0 && pos < cap) D.nbr[(size_t)pos * stride + i] = j;
                     }
-                    n += __popc(m);
+                    n_in += __popc(mi);
+                    n_sh += __popc(m & ~mi);
                 }
             }
+    const int n = n_in + n_sh;
+    // move the shell block [cap - n_sh, cap) down to [n_in, n); the target
+    // starts below the source, so chunks taken in ascending order, each read
+    // in full before it is written, never overwrite an unread entry
+    __syncwarp();
+    if (n < cap) {  // n == cap: already in place; n > cap: overflow, reported below
+        for (int b = 0; b < n_sh; b += 32) {
+            const int k = b + lane;
+            int v = 0;
+            if (k < n_sh) v = D.nbr[(size_t)(cap - n_sh + k) * stride + i];
+            __syncwarp();
+            if (k < n_sh) D.nbr[(size_t)(n_in + k) * stride + i] = v;
+            __syncwarp();
+        }
+    }
     if (lane == 0) {
         D.nnb[i] = min(n, cap);
         if (n > cap) set_err(D, HD_ERR_OVERFLOW, i, r);
     }
 }
 
-__global__ void __launch_bounds__(256) k_nlist(Dev D) {
+__global__ void __launch_bounds__(256, 4) k_nlist(Dev D) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int total = D.rb_off[D.nrep];
     const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -412,10 +436,11 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const int nn = act ? D.nnb[i] : 0;
     const int *nb = D.nbr + i;
     const size_t stride = (size_t)D.natom;
-    // software pipeline: the next neighbour's record is in flight while this one is used
+    // software pipeline: while neighbour k is used, the record of k + 1 and the
+    // index of k + 2 are in flight, so no iteration waits on an index load.
     // plain loads: in the persistent launch the list is rewritten between steps
-    int jn = nn > 0 ? nb[0] : i;
-    AtomRec an = D.rec[jn];
+    AtomRec an = D.rec[nn > 0 ? nb[0] : i];
+    int jn = nn > 1 ? nb[stride] : i;
     // one pair's contribution (cancellation-free LJ form, exact r^2 when the
     // replica's axes share one fixed-point unit)
     auto term = [&](const AtomRec &aj, int ix, int iy, int iz, float dx, float dy, float dz, float r2) {
@@ -445,10 +470,8 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     bool band = false;
     for (int k = 0; k < nn; ++k) {
         const AtomRec aj = an;
-        if (k + 1 < nn) {
-            jn = nb[(size_t)(k + 1) * stride];
-            an = D.rec[jn];
-        }
+        if (k + 1 < nn) an = D.rec[jn];
+        if (k + 2 < nn) jn = nb[(size_t)(k + 2) * stride];
         const int4 pj = aj.p;
         const int ix = (int)((unsigned)pi.x - (unsigned)pj.x);
         const int iy = (int)((unsigned)pi.y - (unsigned)pj.y);
@@ -534,7 +557,7 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
 template <bool Q>
 __global__ void __launch_bounds__(256) k_pair64(Dev D) { dev_pair64<Q>(D, blockIdx.x); }
 template <bool Q>
-__global__ void __launch_bounds__(256) k_pair32(Dev D) { dev_pair32<Q>(D, blockIdx.x); }
+__global__ void __launch_bounds__(256, 4) k_pair32(Dev D) { dev_pair32<Q>(D, blockIdx.x); }
 
 // ---------------------------------------------------------------- per-replica scalars
 // Gathers the replica's tile sums (warp q sums slot q over the tiles in a
