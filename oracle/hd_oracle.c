@@ -458,6 +458,208 @@ void or_hessvec(const or_rep *R, const or_params *P, const double *x, const doub
 }
 
 /* ------------------------------------------------------------------------
+ * Eigenvalue bias (Eq. 13, Eq. 15).  epsilon is the lowest eigenvalue of the
+ * Hessian of V over the motions the model allows.  Reading: fixed atoms do
+ * not move and the rigid layer moves as one body, measured in the same 3N
+ * metric as d and sigma (Eq. 5, Eq. 7: each rigid atom carries the body's
+ * displacement).  The projector P onto those motions zeroes fixed atoms (and
+ * z in 2-D) and replaces every rigid atom's displacement by the layer mean;
+ * epsilon is the lowest eigenvalue of P H P on the range of P.  It is found
+ * by Lanczos iteration with full reorthogonalisation; the lowest eigenvalue
+ * of the tridiagonal matrix by bisection on its Sturm count, its eigenvector
+ * by inverse iteration.  The gradient follows from first-order perturbation
+ * theory: for the unit eigenvector v, grad epsilon = grad (v^T H(r) v) with v
+ * held fixed, a sum over pairs of the third derivative of the pair term.
+ * ---------------------------------------------------------------------- */
+
+/* phi'''(r) of the LJ pair (the shift does not enter). */
+double or_lj3(double r, double eps, double sig) {
+    double sr6 = pow(sig / r, 6.0);
+    double sr12 = sr6 * sr6;
+    return 4.0 * eps * (-2184.0 * sr12 + 336.0 * sr6) / (r * r * r);
+}
+
+void or_project(const or_rep *R, double *u) {
+    int n = R->n, nr = or_nrig(R);
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i)
+        if (R->role[i] == 2)
+            for (int a = 0; a < 3; ++a) m[a] += u[3 * i + a];
+    if (nr > 0)
+        for (int a = 0; a < 3; ++a) m[a] /= (double)nr;
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (R->role[i] == 0 || a >= R->dim) u[3 * i + a] = 0.0;
+            else if (R->role[i] == 2) u[3 * i + a] = m[a];
+        }
+}
+
+static double or_dot(const double *a, const double *b, int N) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += a[k] * b[k];
+    return s;
+}
+
+/* number of eigenvalues of the tridiagonal (alpha, beta) below lam */
+static int or_sturm(const double *al, const double *be, int m, double lam) {
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+        double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+        d = (al[i] - lam) - (i > 0 ? b2 / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++c;
+    }
+    return c;
+}
+
+/* lowest eigenvalue of the tridiagonal matrix and its unit eigenvector y */
+static double or_tri_lowest(const double *al, const double *be, int m, double *y) {
+    double lo = al[0], hi = al[0];
+    for (int i = 0; i < m; ++i) {
+        double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+        lo = fmin(lo, al[i] - r);
+        hi = fmax(hi, al[i] + r);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(1.0, fabs(lo) + fabs(hi)); ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (or_sturm(al, be, m, mid) >= 1) hi = mid;
+        else lo = mid;
+    }
+    double lam = 0.5 * (lo + hi);
+    /* inverse iteration with T - (lam - delta) I, positive definite */
+    double delta = 1e-10 * fmax(1.0, fabs(lam));
+    double *c = malloc(sizeof(double) * m), *dd = malloc(sizeof(double) * m);
+    for (int i = 0; i < m; ++i) y[i] = 1.0;
+    for (int rep = 0; rep < 3; ++rep) {
+        /* forward elimination of the symmetric tridiagonal system */
+        double s = lam - delta;
+        dd[0] = al[0] - s;
+        c[0] = y[0];
+        for (int i = 1; i < m; ++i) {
+            double l = be[i - 1] / dd[i - 1];
+            dd[i] = (al[i] - s) - l * be[i - 1];
+            c[i] = y[i] - l * c[i - 1];
+        }
+        y[m - 1] = c[m - 1] / dd[m - 1];
+        for (int i = m - 2; i >= 0; --i) y[i] = (c[i] - be[i] * y[i + 1]) / dd[i];
+        double nrm = sqrt(or_dot(y, y, m));
+        for (int i = 0; i < m; ++i) y[i] /= nrm;
+    }
+    free(c);
+    free(dd);
+    return lam;
+}
+
+double or_lowest_eig(const or_rep *R, const or_params *P, const double *x, double *v, int maxit, double tol) {
+    int n = R->n, N = 3 * n, nr = or_nrig(R), nmob = 0;
+    for (int i = 0; i < n; ++i) nmob += R->role[i] == 1;
+    int dimP = R->dim * nmob + (nr > 0 ? R->dim : 0);
+    if (maxit > dimP) maxit = dimP;
+    if (maxit < 1) return 0.0;
+    double *Q = malloc(sizeof(double) * (size_t)N * (size_t)(maxit + 1));
+    double *w = malloc(sizeof(double) * N);
+    double *al = malloc(sizeof(double) * maxit), *be = malloc(sizeof(double) * maxit);
+    double *y = malloc(sizeof(double) * maxit);
+    /* start: the given vector (the last eigenvector) plus a fixed generic
+     * vector, so that a new lowest mode after a level crossing is never
+     * missing from the Krylov space; the generic vector alone without one */
+    double *gen = malloc(sizeof(double) * N);
+    for (int k = 0; k < N; ++k) gen[k] = 1.0 + 0.5 * sin(0.7 * (double)k + 0.3 * (double)(k % 7));
+    or_project(R, gen);
+    double ng = sqrt(or_dot(gen, gen, N));
+    memcpy(Q, v, sizeof(double) * N);
+    or_project(R, Q);
+    double nv = sqrt(or_dot(Q, Q, N));
+    for (int k = 0; k < N; ++k) Q[k] = (nv > 1e-12 ? Q[k] / nv : 0.0) + 0.3 * gen[k] / ng;
+    free(gen);
+    double nrm = sqrt(or_dot(Q, Q, N));
+    for (int k = 0; k < N; ++k) Q[k] /= nrm;
+    int m = 0;
+    double lam = 0.0;
+    for (int j = 0; j < maxit; ++j) {
+        double *qj = Q + (size_t)j * N;
+        or_hessvec(R, P, x, qj, w);
+        or_project(R, w);
+        al[j] = or_dot(qj, w, N);
+        for (int k = 0; k < N; ++k) w[k] -= al[j] * qj[k] + (j > 0 ? be[j - 1] * Q[(size_t)(j - 1) * N + k] : 0.0);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i <= j; ++i) {
+                double *qi = Q + (size_t)i * N;
+                double c = or_dot(qi, w, N);
+                for (int k = 0; k < N; ++k) w[k] -= c * qi[k];
+            }
+        be[j] = sqrt(or_dot(w, w, N));
+        m = j + 1;
+        lam = or_tri_lowest(al, be, m, y);
+        if (be[j] * fabs(y[m - 1]) <= tol * fmax(1.0, fabs(lam)) || be[j] < 1e-14 || m == maxit) break;
+        double *qn = Q + (size_t)(j + 1) * N;
+        for (int k = 0; k < N; ++k) qn[k] = w[k] / be[j];
+    }
+    memset(v, 0, sizeof(double) * N);
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < N; ++k) v[k] += y[i] * Q[(size_t)i * N + k];
+    nrm = sqrt(or_dot(v, v, N));
+    for (int k = 0; k < N; ++k) v[k] /= nrm;
+    free(Q); free(w); free(al); free(be); free(y);
+    return lam;
+}
+
+/* g = grad over all 3N coordinates of v^T H(x) v, v held fixed.  Per pair,
+ * with r = x_i - x_j, rho = |r|, w = v_i - v_j, the pair's share is
+ * A |w|^2 + B (r.w)^2 with A = phi'/rho and B = (phi'' - A)/rho^2; since
+ * dA/drho = B rho and dB/drho = (phi''' - 3 B rho)/rho^2, its gradient with
+ * respect to r is r [B |w|^2 + (phi''' - 3 B rho) (r.w)^2 / rho^3]
+ * + 2 B (r.w) w.  The spring's Hessian is constant. */
+void or_eig_grad(const or_rep *R, const or_params *P, const double *x, const double *v, double *g) {
+    int n = R->n;
+    double rc2 = P->rc * P->rc, r[3], ph[3];
+    memset(g, 0, sizeof(double) * 3 * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            double r2 = or_rij(R, x, i, j, r);
+            if (!(r2 < rc2)) continue;
+            double rho = sqrt(r2);
+            int ti = R->type[i], tj = R->type[j];
+            or_lj(rho, R->eps[ti][tj], R->sig[ti][tj], P->rc, ph);
+            double p3 = or_lj3(rho, R->eps[ti][tj], R->sig[ti][tj]);
+            double A = ph[1] / rho, B = (ph[2] - A) / r2;
+            double w[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
+            double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+            double rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+            double cr = B * ww + (p3 - 3.0 * B * rho) * rw * rw / (r2 * rho);
+            for (int a = 0; a < 3; ++a) {
+                double ga = cr * r[a] + 2.0 * B * rw * w[a];
+                g[3 * i + a] += ga;
+                g[3 * j + a] -= ga;
+            }
+        }
+}
+
+/* Eq. 15: out = { DeltaV_2(epsilon), dDeltaV_2/depsilon }, the shape of Eq. 14
+ * with epsilon_L, epsilon_U. */
+void or_dv2(const or_rep *R, double e, double out[2]) {
+    double lo = R->eig_lo, hi = R->eig_hi, dvm = R->dvmax;
+    int m = R->m_exp;
+    if (e >= hi) { out[0] = dvm; out[1] = 0.0; return; }
+    if (e <= lo) { out[0] = 0.0; out[1] = 0.0; return; }
+    double t = (e - hi) / (lo - hi);
+    double tm1 = pow(t, (double)(m - 1));
+    double q = 1.0 - tm1 * t;
+    out[0] = dvm * q * q;
+    out[1] = 2.0 * dvm * q * (-(double)m * tm1) / (lo - hi);
+}
+
+/* Eq. 13: out = { DeltaV, dDeltaV/dDeltaV_1, dDeltaV/dDeltaV_2 }. */
+void or_dv13(const or_rep *R, double dv1, double dv2, double out[3]) {
+    double dvm = R->dvmax;
+    if (!(dvm > 0.0)) { out[0] = 0.0; out[1] = out[2] = 0.0; return; }
+    out[0] = dv1 + dv2 - dv1 * dv2 / dvm;
+    out[1] = 1.0 - dv2 / dvm;
+    out[2] = 1.0 - dv1 / dvm;
+}
+
+/* ------------------------------------------------------------------------
  * Bias.  Eq. 7: d = |r - r_O| over all 3N coordinates (fixed atoms give 0;
  * every rigid atom contributes its own coordinates), s = (r - r_O)/d.
  * Eq. 5: sigma = grad V . s.  Eq. 14: DeltaV = DeltaV_1(sigma).
@@ -476,7 +678,17 @@ double or_bias_potential(const or_rep *R, const or_params *P, const double *x) {
     double d = sqrt(d2);
     double s = d > 0.0 ? G / d : 0.0;
     or_dv1(R, s, out);
-    return P->bias_on ? out[0] : 0.0;
+    if (!P->bias_on) return 0.0;
+    if (!R->eig_on) return out[0];
+    /* Eq. 13 with epsilon at x, Lanczos run to convergence from a copy of
+     * the kept eigenvector */
+    double *v = calloc((size_t)3 * n, sizeof(double)), b2[2], c[3];
+    if (R->veig) memcpy(v, R->veig, sizeof(double) * 3 * n);
+    double e = or_lowest_eig(R, P, x, v, 3 * n, 1e-13);
+    free(v);
+    or_dv2(R, e, b2);
+    or_dv13(R, out[0], b2[0], c);
+    return c[0];
 }
 
 void or_bias_eval(or_rep *R, const or_params *P) {
@@ -500,17 +712,37 @@ void or_bias_eval(or_rep *R, const or_params *P) {
     double bv[2] = {0.0, 0.0};
     if (P->bias_on) or_dv1(R, s, bv);
     R->d = d; R->G = G; R->sigma = s; R->dV = bv[0]; R->dVp = bv[1];
+    R->dV1 = bv[0]; R->dV2 = 0.0; R->dVe = 0.0;
+    /* Eq. 13: DeltaV = DeltaV_1 + DeltaV_2 - DeltaV_1 DeltaV_2 / DeltaV_max,
+     * its force -(dDeltaV/dsigma) grad sigma - (dDeltaV/depsilon) grad epsilon */
+    double *ge = NULL;
+    if (P->bias_on && R->eig_on) {
+        double b2[2], c[3];
+        int maxit = R->eig_maxit > 0 ? R->eig_maxit : 100;
+        R->eig = or_lowest_eig(R, P, R->x, R->veig, maxit, 1e-10);
+        or_dv2(R, R->eig, b2);
+        or_dv13(R, bv[0], b2[0], c);
+        R->dV2 = b2[0];
+        R->dV = c[0];
+        R->dVp = c[1] * bv[1];
+        R->dVe = c[2] * b2[1];
+        if (R->dVe != 0.0) {
+            ge = malloc(sizeof(double) * 3 * n);
+            or_eig_grad(R, P, R->x, R->veig, ge);
+        }
+    }
     R->fbody[0] = R->fbody[1] = R->fbody[2] = 0.0;
     for (int i = 0; i < n; ++i) {
         or_disp(R, R->x, i, dr);
         for (int a = 0; a < 3; ++a) {
             double g = -R->f_lj[3 * i + a] + (R->role[i] == 2 ? gs[a] / (double)nr : 0.0);
             double gsig = d > 0.0 ? (R->hdr[3 * i + a] + g) / d - s * dr[a] / (d * d) : 0.0;
-            double ft = -g - bv[1] * gsig;
+            double ft = -g - R->dVp * gsig - (ge ? R->dVe * ge[3 * i + a] : 0.0);
             R->ftot[3 * i + a] = ft;
             if (R->role[i] == 2) R->fbody[a] += ft;
         }
     }
+    free(ge);
     for (int a = 0; a < 3; ++a) R->xT[a] = xt[a];
     R->V = R->V_lj + (nr > 0 ? or_ext_energy(R, xt) : 0.0);
     R->FR = R->kspring * (R->slider[0] - xt[0]);          /* Eq. 10 */

@@ -11,7 +11,9 @@
  *     shifted so that it is zero there;
  *   - the local slope sigma = grad V . s (Eq. 5), the distance d (Eq. 7) and
  *     the direction s = (r - r_O)/d defined after Eq. 7;
- *   - the slope bias DeltaV_1(sigma), Eq. 14 (Eq. 13 with DeltaV_2 = 0);
+ *   - the slope bias DeltaV_1(sigma), Eq. 14, alone (Eq. 13 with DeltaV_2 = 0)
+ *     or combined by Eq. 13 with the eigenvalue bias DeltaV_2(epsilon),
+ *     Eq. 15, epsilon the lowest eigenvalue of the Hessian;
  *   - the boosted clock sum of exp(beta DeltaV) dt, Eq. 3;
  *   - the rigid top layer pulled by the slider spring and the normal load
  *     (Sec. 3.1.1, Sec. 3.2.1), lateral force F_R = k (x_S - x_T), Eq. 10;
@@ -49,6 +51,11 @@ typedef struct {
     double vbody[3];
     /* scalars at the current positions */
     double V, V_lj, K, dV, dVp, sigma, d, G, xT[3], fbody[3], FR;
+    /* eigenvalue bias, Eq. 13 and Eq. 15 (eig_on = 0: the slope bias alone) */
+    int eig_on, eig_maxit;            /* Lanczos steps per evaluation, at most */
+    double eig_lo, eig_hi;            /* epsilon_L, epsilon_U */
+    double *veig;                     /* [n][3] lowest eigenvector, kept as the next start */
+    double eig, dV1, dV2, dVe;        /* epsilon, DeltaV_1, DeltaV_2, dDeltaV/depsilon */
 } or_rep;
 
 typedef struct {
@@ -80,6 +87,12 @@ int    or_quench(or_rep *R, const or_params *P, int method, double ftol, int max
 int    or_quench_batch(or_rep *reps, int nrep, const or_params *P, int method, double ftol,
                        int max_iter, double step_size, double **xq, double *fmax_out, int *iters);
 int    or_transition(const or_rep *R, const double *xq, double theta, double *maxdisp);
+double or_lj3(double r, double eps, double sig);
+void   or_project(const or_rep *R, double *u);
+double or_lowest_eig(const or_rep *R, const or_params *P, const double *x, double *v, int maxit, double tol);
+void   or_eig_grad(const or_rep *R, const or_params *P, const double *x, const double *v, double *g);
+void   or_dv2(const or_rep *R, double e, double out[2]);
+void   or_dv13(const or_rep *R, double dv1, double dv2, double out[3]);
 int    or_num_threads(void);
 
 #endif

@@ -55,6 +55,9 @@ class OrRep(C.Structure):
         ("V", C.c_double), ("V_lj", C.c_double), ("K", C.c_double), ("dV", C.c_double),
         ("dVp", C.c_double), ("sigma", C.c_double), ("d", C.c_double), ("G", C.c_double),
         ("xT", C.c_double * 3), ("fbody", C.c_double * 3), ("FR", C.c_double),
+        ("eig_on", C.c_int), ("eig_maxit", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
+        ("veig", C.POINTER(C.c_double)),
+        ("eig", C.c_double), ("dV1", C.c_double), ("dV2", C.c_double), ("dVe", C.c_double),
     ]
 
 
@@ -99,6 +102,14 @@ def lib():
         L.or_transition.argtypes = [rp, dp, C.c_double, dp]
         L.or_transition.restype = C.c_int
         L.or_num_threads.restype = C.c_int
+        L.or_lj3.argtypes = [C.c_double] * 3
+        L.or_lj3.restype = C.c_double
+        L.or_project.argtypes = [rp, dp]
+        L.or_lowest_eig.argtypes = [rp, pp, dp, dp, C.c_int, C.c_double]
+        L.or_lowest_eig.restype = C.c_double
+        L.or_eig_grad.argtypes = [rp, pp, dp, dp, dp]
+        L.or_dv2.argtypes = [rp, C.c_double, dp]
+        L.or_dv13.argtypes = [rp, C.c_double, C.c_double, dp]
         _lib = L
     return _lib
 
@@ -172,6 +183,12 @@ class OracleReplica:
         s.xb = _dp(self.xb)
         s.f_lj, s.hdr, s.e_atom, s.ftot = _dp(self.f_lj), _dp(self.hdr), _dp(self.e_atom), _dp(self.ftot)
         s.t_h, s.t_md, s.step = rep.t_h0, rep.t_md0, int(rep.step0)
+        # eigenvalue bias (Eq. 13, Eq. 15): off unless the replica asks for it
+        self.veig = np.zeros((n, 3))
+        s.eig_on = int(getattr(rep, "eig_on", 0))
+        s.eig_maxit = int(getattr(rep, "eig_maxit", 100))
+        s.eig_lo, s.eig_hi = float(getattr(rep, "eig_lo", 0.0)), float(getattr(rep, "eig_hi", 1.0))
+        s.veig = _dp(self.veig)
         self.s = s
         self.rep = rep
         if draw_velocities is None:
@@ -253,6 +270,38 @@ class OracleReplica:
         it = lib().or_quench(C.byref(self.s), C.byref(self.P), int(method), float(ftol), int(max_iter),
                              float(step_size), _dp(xq), _dp(fmax))
         return xq, int(it), float(fmax[0])
+
+    # ---- eigenvalue bias (Eq. 13, Eq. 15) ----
+    def project(self, u):
+        """P u: fixed atoms (and z in 2-D) zeroed, rigid atoms set to the layer mean."""
+        u = np.ascontiguousarray(u, dtype=np.float64).copy()
+        lib().or_project(C.byref(self.s), _dp(u))
+        return u
+
+    def lowest_eig(self, x=None, v0=None, maxit=None, tol=1e-12):
+        """(epsilon, v): lowest eigenvalue of P H P on the range of P at x (Lanczos)."""
+        x = self.x if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        v = np.zeros((self.n, 3)) if v0 is None else np.ascontiguousarray(v0, dtype=np.float64).copy()
+        e = lib().or_lowest_eig(C.byref(self.s), C.byref(self.P), _dp(x), _dp(v), int(maxit or 3 * self.n), tol)
+        return e, v
+
+    def eig_grad(self, v, x=None):
+        """grad of v^T H(x) v over all 3N coordinates, v fixed."""
+        x = self.x if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        g = np.zeros((self.n, 3))
+        lib().or_eig_grad(C.byref(self.s), C.byref(self.P), _dp(x), _dp(v), _dp(g))
+        return g
+
+    def dv2(self, e):
+        out = np.zeros(2)
+        lib().or_dv2(C.byref(self.s), float(e), _dp(out))
+        return out
+
+    def dv13(self, dv1, dv2):
+        out = np.zeros(3)
+        lib().or_dv13(C.byref(self.s), float(dv1), float(dv2), _dp(out))
+        return out
 
     def transition(self, xq, theta=0.5):
         md = np.zeros(1)

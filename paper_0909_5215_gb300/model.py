@@ -74,6 +74,12 @@ class Replica:
     t_h0: float = 0.0
     t_md0: float = 0.0
     step0: int = 0
+    # eigenvalue bias (Eq. 13, Eq. 15): band [eig_lo, eig_hi] of the lowest
+    # Hessian eigenvalue; evaluated by the CPU oracle only so far
+    eig_on: int = 0
+    eig_lo: float = 0.0
+    eig_hi: float = 1.0
+    eig_maxit: int = 100
 
     @property
     def n(self) -> int:

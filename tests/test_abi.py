@@ -131,3 +131,16 @@ def test_binding_fails_loudly_without_library(hdlib, monkeypatch):
     monkeypatch.setattr(hdlib, "_lib", None)
     with pytest.raises(RuntimeError):
         hdlib.lib()
+
+
+def test_eigenvalue_bias_is_refused_not_dropped():
+    """The library computes the slope bias only: a replica asking for the
+    eigenvalue term is refused before anything reaches the device."""
+    from conftest import small2d
+    from paper_0909_5215_gb300 import hd
+    r = small2d()
+    r.eig_on = 1
+    with pytest.raises(hd.HdError) as ei:
+        hd.make_descs([r])
+    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
+    hd.make_descs([small2d()])
