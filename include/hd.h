@@ -65,7 +65,8 @@ typedef enum {
 typedef enum { HD_FP64 = 0, HD_FP32_SPLIT = 1 } hd_precision;
 
 typedef enum {
-    HD_DRIVER_AUTO = 0,        /* persistent when it fits, else per-phase kernels    */
+    HD_DRIVER_AUTO = 0,        /* the per-phase kernels; pick by measurement instead
+                                  (the Python autotuner times both drivers)           */
     HD_DRIVER_KERNELS = 1,     /* one kernel per phase, captured in a CUDA graph     */
     HD_DRIVER_PERSISTENT = 2   /* one cooperative launch steps every replica         */
 } hd_driver;
