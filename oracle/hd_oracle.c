@@ -857,6 +857,8 @@ void or_run(or_rep *R, const or_params *P, int nsteps) {
             or_nlist_cells(R, P->rc + P->skin);
             R->n_rebuild += 1;
         }
+        if (R->vslide != 0.0)          /* continuous sliding: the slider at the step's end */
+            R->slider[0] = R->slide_x0 + (double)(R->step + 1 - R->slide_step0) * (R->vslide * h);
         or_forces(R, P);
         or_bias_eval(R, P);
         /* B */

@@ -56,6 +56,11 @@ typedef struct {
     double eig_lo, eig_hi;            /* epsilon_L, epsilon_U */
     double *veig;                     /* [n][3] lowest eigenvector, kept as the next start */
     double eig, dV1, dV2, dVe;        /* epsilon, DeltaV_1, DeltaV_2, dDeltaV/depsilon */
+    /* continuous sliding (Sec. 3.1.1, method 1): with vslide != 0 the slider
+     * moves along x every step, x_S = slide_x0 + k (vslide dt) after the k-th
+     * step since slide_step0; vslide = 0 keeps it where it is */
+    double vslide, slide_x0;
+    int64_t slide_step0;
 } or_rep;
 
 typedef struct {

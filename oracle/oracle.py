@@ -58,6 +58,7 @@ class OrRep(C.Structure):
         ("eig_on", C.c_int), ("eig_maxit", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
         ("veig", C.POINTER(C.c_double)),
         ("eig", C.c_double), ("dV1", C.c_double), ("dV2", C.c_double), ("dVe", C.c_double),
+        ("vslide", C.c_double), ("slide_x0", C.c_double), ("slide_step0", C.c_int64),
     ]
 
 
@@ -189,6 +190,9 @@ class OracleReplica:
         s.eig_maxit = int(getattr(rep, "eig_maxit", 100))
         s.eig_lo, s.eig_hi = float(getattr(rep, "eig_lo", 0.0)), float(getattr(rep, "eig_hi", 1.0))
         s.veig = _dp(self.veig)
+        # continuous sliding: slider x = x_S0 + k (v dt) after the k-th step from here
+        s.vslide = float(getattr(rep, "v_slide", 0.0))
+        s.slide_x0, s.slide_step0 = float(rep.slider[0]), int(rep.step0)
         self.s = s
         self.rep = rep
         if draw_velocities is None:

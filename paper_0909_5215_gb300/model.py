@@ -80,6 +80,9 @@ class Replica:
     eig_lo: float = 0.0
     eig_hi: float = 1.0
     eig_maxit: int = 100
+    # continuous sliding (slider moving at v_slide along x every step);
+    # evaluated by the CPU oracle only so far
+    v_slide: float = 0.0
 
     @property
     def n(self) -> int:

@@ -144,3 +144,13 @@ def test_eigenvalue_bias_is_refused_not_dropped():
         hd.make_descs([r])
     assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
     hd.make_descs([small2d()])
+
+
+def test_continuous_sliding_is_refused_not_dropped():
+    from conftest import small2d
+    from paper_0909_5215_gb300 import hd
+    r = small2d()
+    r.v_slide = 1e-3
+    with pytest.raises(hd.HdError) as ei:
+        hd.make_descs([r])
+    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
