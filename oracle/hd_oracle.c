@@ -127,6 +127,19 @@ static void or_disp(const or_rep *R, const double *x, int i, double dr[3]) {
         dr[a] = or_mi(x[3 * i + a] - R->xo[3 * i + a], R->L[a], R->periodic[a]);
 }
 
+/* Eq. 12: out = { phi, phi', phi'' } of the harmonic bond; phi''' = 0. */
+static void or_bond(const or_rep *R, double r, double out[3]) {
+    double d = r - R->rbond;
+    out[0] = 0.5 * R->kbond * d * d;
+    out[1] = R->kbond * d;
+    out[2] = R->kbond;
+}
+
+/* The LJ term acts between i and j unless both are atoms of a bonded tip. */
+static int or_lj_on(const or_rep *R, int i, int j) {
+    return !(R->nbond > 0 && R->type[i] == 1 && R->type[j] == 1);
+}
+
 /* ------------------------------------------------------------------------
  * Rigid top layer, slider spring and normal load (Sec. 3.1.1, Sec. 3.2.1).
  * x_T is the centre of the rigid layer.  The spring pulls x_T toward x_S
@@ -312,7 +325,7 @@ static double or_pairs_on_list(const or_rep *R, const double *x, const int *nnb,
         for (int k = 0; k < nnb[i]; ++k) {
             int j = nbr[(size_t)i * R->maxnb + k];
             double r2 = or_rij(R, x, i, j, r);
-            if (!(r2 < rc2)) continue;
+            if (!(r2 < rc2) || !or_lj_on(R, i, j)) continue;
             int tj = R->type[j];
             double rr = sqrt(r2);
             or_lj(rr, R->eps[ti][tj], R->sig[ti][tj], rc, ph);
@@ -325,6 +338,29 @@ static double or_pairs_on_list(const or_rep *R, const double *x, const int *nnb,
                 double du[3] = {dri[0] - drj[0], dri[1] - drj[1], dri[2] - drj[2]};
                 double rdu = r[0] * du[0] + r[1] * du[1] + r[2] * du[2];
                 for (int a = 0; a < 3; ++a) hdr[3 * i + a] += A * du[a] + B * rdu * r[a];
+            }
+        }
+    }
+    /* bonds (Eq. 12), each pair once, both atoms updated */
+    for (int b = 0; b < R->nbond; ++b) {
+        int i = R->bonds[2 * b], j = R->bonds[2 * b + 1];
+        double r2 = or_rij(R, x, i, j, r), rr = sqrt(r2);
+        or_bond(R, rr, ph);
+        double A = ph[1] / rr, B = (ph[2] - A) / r2;
+        for (int a = 0; a < 3; ++a) {
+            f[3 * i + a] -= A * r[a];
+            f[3 * j + a] += A * r[a];
+        }
+        if (e_atom) { e_atom[i] += 0.5 * ph[0]; e_atom[j] += 0.5 * ph[0]; }
+        if (hdr) {
+            or_disp(R, x, i, dri);
+            or_disp(R, x, j, drj);
+            double du[3] = {dri[0] - drj[0], dri[1] - drj[1], dri[2] - drj[2]};
+            double rdu = r[0] * du[0] + r[1] * du[1] + r[2] * du[2];
+            for (int a = 0; a < 3; ++a) {
+                double h = A * du[a] + B * rdu * r[a];
+                hdr[3 * i + a] += h;
+                hdr[3 * j + a] -= h;
             }
         }
     }
@@ -365,7 +401,7 @@ double or_forces_brute(const or_rep *R, const or_params *P, double *f, double *e
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
             double r2 = or_rij(R, R->x, i, j, r);
-            if (!(r2 < rc2)) continue;
+            if (!(r2 < rc2) || !or_lj_on(R, i, j)) continue;
             double rr = sqrt(r2);
             or_lj(rr, R->eps[R->type[i]][R->type[j]], R->sig[R->type[i]][R->type[j]], P->rc, ph);
             for (int a = 0; a < 3; ++a) {
@@ -376,6 +412,18 @@ double or_forces_brute(const or_rep *R, const or_params *P, double *f, double *e
             vtot += ph[0];
             if (e_atom) { e_atom[i] += 0.5 * ph[0]; e_atom[j] += 0.5 * ph[0]; }
         }
+    for (int b = 0; b < R->nbond; ++b) {
+        int i = R->bonds[2 * b], j = R->bonds[2 * b + 1];
+        double rr = sqrt(or_rij(R, R->x, i, j, r));
+        or_bond(R, rr, ph);
+        for (int a = 0; a < 3; ++a) {
+            double fa = -ph[1] * r[a] / rr;
+            f[3 * i + a] += fa;
+            f[3 * j + a] -= fa;
+        }
+        vtot += ph[0];
+        if (e_atom) { e_atom[i] += 0.5 * ph[0]; e_atom[j] += 0.5 * ph[0]; }
+    }
     return vtot;
 }
 
@@ -386,10 +434,14 @@ double or_potential(const or_rep *R, const or_params *P, const double *x) {
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
             double r2 = or_rij(R, x, i, j, r);
-            if (!(r2 < rc2)) continue;
+            if (!(r2 < rc2) || !or_lj_on(R, i, j)) continue;
             or_lj(sqrt(r2), R->eps[R->type[i]][R->type[j]], R->sig[R->type[i]][R->type[j]], P->rc, ph);
             v += ph[0];
         }
+    for (int b = 0; b < R->nbond; ++b) {
+        or_bond(R, sqrt(or_rij(R, x, R->bonds[2 * b], R->bonds[2 * b + 1], r)), ph);
+        v += ph[0];
+    }
     if (or_nrig(R) > 0) {
         or_tip_centre(R, x, xt);
         v += or_ext_energy(R, xt);
@@ -405,7 +457,7 @@ void or_gradient(const or_rep *R, const or_params *P, const double *x, double *g
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
             double r2 = or_rij(R, x, i, j, r);
-            if (!(r2 < rc2)) continue;
+            if (!(r2 < rc2) || !or_lj_on(R, i, j)) continue;
             double rr = sqrt(r2);
             or_lj(rr, R->eps[R->type[i]][R->type[j]], R->sig[R->type[i]][R->type[j]], P->rc, ph);
             for (int a = 0; a < 3; ++a) {
@@ -414,6 +466,16 @@ void or_gradient(const or_rep *R, const or_params *P, const double *x, double *g
                 g[3 * j + a] -= ga;
             }
         }
+    for (int b = 0; b < R->nbond; ++b) {
+        int i = R->bonds[2 * b], j = R->bonds[2 * b + 1];
+        double rr = sqrt(or_rij(R, x, i, j, r));
+        or_bond(R, rr, ph);
+        for (int a = 0; a < 3; ++a) {
+            double ga = ph[1] * r[a] / rr;
+            g[3 * i + a] += ga;
+            g[3 * j + a] -= ga;
+        }
+    }
     if (nr > 0) {
         double xt[3], gs[3];
         or_tip_centre(R, x, xt);
@@ -432,7 +494,7 @@ void or_hessvec(const or_rep *R, const or_params *P, const double *x, const doub
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
             double r2 = or_rij(R, x, i, j, r);
-            if (!(r2 < rc2)) continue;
+            if (!(r2 < rc2) || !or_lj_on(R, i, j)) continue;
             double rr = sqrt(r2);
             or_lj(rr, R->eps[R->type[i]][R->type[j]], R->sig[R->type[i]][R->type[j]], P->rc, ph);
             double A = ph[1] / rr, B = (ph[2] - A) / r2;
@@ -444,6 +506,19 @@ void or_hessvec(const or_rep *R, const or_params *P, const double *x, const doub
                 out[3 * j + a] -= h;
             }
         }
+    for (int b = 0; b < R->nbond; ++b) {
+        int i = R->bonds[2 * b], j = R->bonds[2 * b + 1];
+        double r2 = or_rij(R, x, i, j, r), rr = sqrt(r2);
+        or_bond(R, rr, ph);
+        double A = ph[1] / rr, B = (ph[2] - A) / r2;
+        double du[3] = {u[3 * i] - u[3 * j], u[3 * i + 1] - u[3 * j + 1], u[3 * i + 2] - u[3 * j + 2]};
+        double rdu = r[0] * du[0] + r[1] * du[1] + r[2] * du[2];
+        for (int a = 0; a < 3; ++a) {
+            double h = A * du[a] + B * rdu * r[a];
+            out[3 * i + a] += h;
+            out[3 * j + a] -= h;
+        }
+    }
     if (nr > 0) {
         double sx = 0.0, sy = 0.0;
         for (int i = 0; i < n; ++i)
@@ -611,6 +686,21 @@ double or_lowest_eig(const or_rep *R, const or_params *P, const double *x, doubl
  * dA/drho = B rho and dB/drho = (phi''' - 3 B rho)/rho^2, its gradient with
  * respect to r is r [B |w|^2 + (phi''' - 3 B rho) (r.w)^2 / rho^3]
  * + 2 B (r.w) w.  The spring's Hessian is constant. */
+static void or_eig_grad_pair(const double r[3], double r2, const double ph[3], double p3, const double *v, int i,
+                             int j, double *g) {
+    double rho = sqrt(r2);
+    double A = ph[1] / rho, B = (ph[2] - A) / r2;
+    double w[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
+    double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+    double cr = B * ww + (p3 - 3.0 * B * rho) * rw * rw / (r2 * rho);
+    for (int a = 0; a < 3; ++a) {
+        double ga = cr * r[a] + 2.0 * B * rw * w[a];
+        g[3 * i + a] += ga;
+        g[3 * j + a] -= ga;
+    }
+}
+
 void or_eig_grad(const or_rep *R, const or_params *P, const double *x, const double *v, double *g) {
     int n = R->n;
     double rc2 = P->rc * P->rc, r[3], ph[3];
@@ -618,22 +708,18 @@ void or_eig_grad(const or_rep *R, const or_params *P, const double *x, const dou
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) {
             double r2 = or_rij(R, x, i, j, r);
-            if (!(r2 < rc2)) continue;
+            if (!(r2 < rc2) || !or_lj_on(R, i, j)) continue;
             double rho = sqrt(r2);
             int ti = R->type[i], tj = R->type[j];
             or_lj(rho, R->eps[ti][tj], R->sig[ti][tj], P->rc, ph);
-            double p3 = or_lj3(rho, R->eps[ti][tj], R->sig[ti][tj]);
-            double A = ph[1] / rho, B = (ph[2] - A) / r2;
-            double w[3] = {v[3 * i] - v[3 * j], v[3 * i + 1] - v[3 * j + 1], v[3 * i + 2] - v[3 * j + 2]};
-            double ww = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-            double rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
-            double cr = B * ww + (p3 - 3.0 * B * rho) * rw * rw / (r2 * rho);
-            for (int a = 0; a < 3; ++a) {
-                double ga = cr * r[a] + 2.0 * B * rw * w[a];
-                g[3 * i + a] += ga;
-                g[3 * j + a] -= ga;
-            }
+            or_eig_grad_pair(r, r2, ph, or_lj3(rho, R->eps[ti][tj], R->sig[ti][tj]), v, i, j, g);
         }
+    for (int b = 0; b < R->nbond; ++b) {            /* Eq. 12: phi''' = 0 */
+        int i = R->bonds[2 * b], j = R->bonds[2 * b + 1];
+        double r2 = or_rij(R, x, i, j, r);
+        or_bond(R, sqrt(r2), ph);
+        or_eig_grad_pair(r, r2, ph, 0.0, v, i, j, g);
+    }
 }
 
 /* Eq. 15: out = { DeltaV_2(epsilon), dDeltaV_2/depsilon }, the shape of Eq. 14

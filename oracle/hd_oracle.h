@@ -15,6 +15,8 @@
  *     or combined by Eq. 13 with the eigenvalue bias DeltaV_2(epsilon),
  *     Eq. 15, epsilon the lowest eigenvalue of the Hessian;
  *   - the boosted clock sum of exp(beta DeltaV) dt, Eq. 3;
+ *   - optional harmonic bonds between tip atoms in place of their LJ term,
+ *     Eq. 12 (the 3-D model of Sec. 3.2.1);
  *   - the rigid top layer pulled by the slider spring and the normal load
  *     (Sec. 3.1.1, Sec. 3.2.1), lateral force F_R = k (x_S - x_T), Eq. 10;
  *   - Langevin BAOAB dynamics with Philox4x32-10 noise, steepest-descent and
@@ -61,6 +63,11 @@ typedef struct {
      * step since slide_step0; vslide = 0 keeps it where it is */
     double vslide, slide_x0;
     int64_t slide_step0;
+    /* harmonic tip bonds, Eq. 12 (Sec. 3.2.1): nbond pairs i, j bonded by
+     * kbond (r - rbond)^2 / 2; with nbond > 0 tip-tip pairs have no LJ term */
+    int nbond;
+    const int *bonds;                 /* [nbond][2] */
+    double kbond, rbond;
 } or_rep;
 
 typedef struct {

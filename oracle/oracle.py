@@ -59,6 +59,7 @@ class OrRep(C.Structure):
         ("veig", C.POINTER(C.c_double)),
         ("eig", C.c_double), ("dV1", C.c_double), ("dV2", C.c_double), ("dVe", C.c_double),
         ("vslide", C.c_double), ("slide_x0", C.c_double), ("slide_step0", C.c_int64),
+        ("nbond", C.c_int), ("bonds", C.POINTER(C.c_int)), ("kbond", C.c_double), ("rbond", C.c_double),
     ]
 
 
@@ -193,6 +194,12 @@ class OracleReplica:
         # continuous sliding: slider x = x_S0 + k (v dt) after the k-th step from here
         s.vslide = float(getattr(rep, "v_slide", 0.0))
         s.slide_x0, s.slide_step0 = float(rep.slider[0]), int(rep.step0)
+        # harmonic tip bonds (Eq. 12); none: every pair is LJ
+        b = getattr(rep, "bonds", None)
+        self.bonds = np.zeros((0, 2), np.int32) if b is None else np.ascontiguousarray(b, dtype=np.int32).reshape(-1, 2)
+        s.nbond = len(self.bonds)
+        s.bonds = self.bonds.ctypes.data_as(C.POINTER(C.c_int))
+        s.kbond, s.rbond = float(getattr(rep, "k_bond", 57.2)), float(getattr(rep, "r_bond", 1.12))
         self.s = s
         self.rep = rep
         if draw_velocities is None:

@@ -177,12 +177,15 @@ def make_params(params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, pre
 def make_descs(reps):
     """Build the C descriptors; returns (array, keep-alive list).  Replicas
     asking for what the library does not compute (the eigenvalue bias of
-    Eq. 13/15, continuous sliding) are refused rather than run without it."""
+    Eq. 13/15, continuous sliding, harmonic tip bonds of Eq. 12) are refused
+    rather than run without it."""
     for k, r in enumerate(reps):
         if getattr(r, "eig_on", 0):
             raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: the eigenvalue bias is not implemented on the GPU" % k)
         if getattr(r, "v_slide", 0.0):
             raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: continuous sliding is not implemented on the GPU" % k)
+        if getattr(r, "bonds", None) is not None and len(r.bonds):
+            raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: harmonic tip bonds are not implemented on the GPU" % k)
     keep = []
     arr = (hd_replica_desc * len(reps))()
 

@@ -83,6 +83,12 @@ class Replica:
     # continuous sliding (slider moving at v_slide along x every step);
     # evaluated by the CPU oracle only so far
     v_slide: float = 0.0
+    # harmonic tip bonds (Eq. 12): (m, 2) atom pairs bonded by
+    # k_bond (r - r_bond)^2 / 2; with bonds the tip-tip LJ term is dropped.
+    # Evaluated by the CPU oracle only so far.
+    bonds: np.ndarray | None = None
+    k_bond: float = 57.2
+    r_bond: float = 1.12
 
     @property
     def n(self) -> int:
@@ -209,6 +215,102 @@ def afm3d(nx: int = 24, ny: int = 24, nz: int = 6, n_fixed_layers: int = 2,
     role = np.concatenate([sub_role, tip_role]).astype(np.uint8)
     typ = np.concatenate([np.full(len(sub), TYPE_SUB), np.full(len(tip), TYPE_TIP)]).astype(np.uint8)
     return _finish(3, pos, role, typ, (nx * a, ny * a, 0.0), (1, 1, 0), **kw)
+
+
+def paper2d(**kw) -> Replica:
+    """The paper's own 2-D model (Sec. 3.1.1): 80 substrate and 33 tip atoms,
+    k = 5, F_N = 5, eps_ts = 0.5.  Reading (the figure is not available): the
+    substrate is 20 columns x 4 rows of the triangular lattice with the bottom
+    row fixed; the tip is an inverted trapezoid of rows holding 3, 4, ..., 8
+    atoms on the lattice sites continued above the substrate (so its contact
+    row is in registry), the top row of 8 rigid."""
+    n_cols, n_rows = 20, 4
+    dy = A2D * math.sqrt(3.0) / 2.0
+    lx = n_cols * A2D
+    sub = np.array([((i + 0.5 * (j % 2)) * A2D, j * dy) for j in range(n_rows) for i in range(n_cols)])
+    sub_role = np.where(np.arange(len(sub)) < n_cols, ROLE_FIXED, ROLE_MOBILE)
+    ja = n_rows
+    ia = int(round(lx / 2.0 / A2D - 0.5 * (ja % 2)))
+    xc = (ia + 0.5 * (ja % 2)) * A2D
+    tip, tip_role = [], []
+    for k, m in enumerate(range(3, 9)):
+        for q in range(m):
+            tip.append((xc + (q - 0.5 * (m - 1)) * A2D, (ja + k) * dy))
+            tip_role.append(ROLE_RIGID if m == 8 else ROLE_MOBILE)
+    tip = np.array(tip)
+    pos = np.zeros((len(sub) + len(tip), 3))
+    pos[: len(sub), :2] = sub
+    pos[len(sub):, :2] = tip
+    role = np.concatenate([sub_role, tip_role]).astype(np.uint8)
+    typ = np.concatenate([np.full(len(sub), TYPE_SUB), np.full(len(tip), TYPE_TIP)]).astype(np.uint8)
+    kw.setdefault("k_spring", 5.0)
+    kw.setdefault("f_normal", 5.0)
+    kw.setdefault("eps", PAPER_EPS_2D)
+    return _finish(2, pos, role, typ, (lx, 0.0, 0.0), (1, 0, 0), **kw)
+
+
+def tip_bonds(rep: Replica, cut: float = 1.3) -> np.ndarray:
+    """Nearest-neighbour pairs of tip atoms (distance < cut) in the given
+    configuration, each once (i < j)."""
+    t = np.nonzero(rep.type == TYPE_TIP)[0]
+    x = rep.pos[t]
+    d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1)
+    a, b = np.nonzero(np.triu(d2 < cut * cut, 1))
+    return np.stack([t[a], t[b]], 1).astype(np.int32)
+
+
+def paper3d(**kw) -> Replica:
+    """The paper's own 3-D model (Sec. 3.2.1): 1800 fcc substrate atoms and a
+    183-atom tip joined along [001], k = 10, F_N = 5, eps_st = 0.2, tip atoms
+    held together by harmonic bonds (Eq. 12, k = 57.2, r_O = 1.12) instead of
+    LJ.  Reading (the figure is not available): the substrate is 15 x 15 x 2
+    cubic cells (four atomic layers, the bottom one fixed); the tip is a cone
+    with flat ends on the fcc sites continued above the substrate: in the
+    k-th layer (k = 0 at the contact) the sites within 1.08 a + 0.42 a k of
+    the axis, which gives layers of 9, 16, 21, 32, 45 and 60 atoms (the nine
+    contact atoms in registry with the substrate), the top layer rigid; bonds
+    join tip atoms at the nearest-neighbour distance."""
+    a = AFCC
+    nx = ny = 15
+    basis = np.array([(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)])
+    g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(2), indexing="ij"), -1).reshape(-1, 3)
+    sub = ((g[:, None, :] + basis[None]) * a).reshape(-1, 3)
+    layer = np.rint(sub[:, 2] / (a / 2)).astype(int)
+    sub_role = np.where(layer < 1, ROLE_FIXED, ROLE_MOBILE)
+    za = sub[:, 2].max() + a / 2
+    # apex: the site of the first layer above the substrate nearest the centre
+    k0 = int(round(za / (a / 2)))
+    cx, cy = nx * a / 2, ny * a / 2
+    best = None
+    for i in range(2 * nx):
+        for j in range(2 * ny):
+            if (i + j + k0) % 2 == 0:
+                d = (i * a / 2 - cx) ** 2 + (j * a / 2 - cy) ** 2
+                if best is None or d < best[0]:
+                    best = (d, i, j)
+    _, i0, j0 = best
+    tip, tip_role = [], []
+    for k in range(6):
+        rmax = 1.08 * a + 0.42 * a * k
+        n = int(rmax / (a / 2)) + 1
+        for i in range(i0 - n, i0 + n + 1):
+            for j in range(j0 - n, j0 + n + 1):
+                if (i + j + k0 + k) % 2:
+                    continue
+                dx, dy2 = (i - i0) * a / 2, (j - j0) * a / 2
+                if dx * dx + dy2 * dy2 <= rmax * rmax * (1 + 1e-12):
+                    tip.append((i * a / 2, j * a / 2, za + k * a / 2))
+                    tip_role.append(ROLE_RIGID if k == 5 else ROLE_MOBILE)
+    tip = np.array(tip)
+    pos = np.concatenate([sub, tip])
+    role = np.concatenate([sub_role, tip_role]).astype(np.uint8)
+    typ = np.concatenate([np.full(len(sub), TYPE_SUB), np.full(len(tip), TYPE_TIP)]).astype(np.uint8)
+    kw.setdefault("k_spring", 10.0)
+    kw.setdefault("f_normal", 5.0)
+    kw.setdefault("eps", PAPER_EPS_3D)
+    rep = _finish(3, pos, role, typ, (nx * a, ny * a, 0.0), (1, 1, 0), **kw)
+    rep.bonds = tip_bonds(rep)
+    return rep
 
 
 # --------------------------------------------------------------------------

@@ -154,3 +154,11 @@ def test_continuous_sliding_is_refused_not_dropped():
     with pytest.raises(hd.HdError) as ei:
         hd.make_descs([r])
     assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
+
+
+def test_tip_bonds_are_refused_not_dropped():
+    from paper_0909_5215_gb300 import hd
+    from paper_0909_5215_gb300 import model as M
+    with pytest.raises(hd.HdError) as ei:
+        hd.make_descs([M.paper3d()])
+    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
