@@ -888,6 +888,77 @@ void or_init(or_rep *R, const or_params *P, int draw_velocities) {
  * DeltaV of the configuration the step starts from.
  * Verlet list rebuilt when any atom has moved more than skin/2.
  * ---------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------
+ * Nose-Hoover chain (Sec. 3.1.1 names the chain thermostat; the integrator
+ * is the reversible Trotter splitting of Martyna, Tuckerman, Tobias & Klein,
+ * Mol. Phys. 87 (1996) 1117, one stage): a half step of the chain before the
+ * first kick and after the last.  Thermostat j has mass Q_j, position xi_j,
+ * velocity v_j and force G_1 = (2K_m - N_f kT)/Q_1 (K_m the kinetic energy
+ * of the mobile atoms), G_j = (Q_{j-1} v_{j-1}^2 - kT)/Q_j; the chain end
+ * is updated first, each v_j between two damping factors exp(-v_{j+1} dt/8)
+ * from the end down to 1, the mobile velocities are scaled by
+ * exp(-v_1 dt/2), the xi advance by v dt/2, and the sweep is repeated from
+ * 1 back up to the end.  The extended energy K + V + DeltaV + sum Q v^2/2
+ * + N_f kT xi_1 + kT sum_{j>1} xi_j is conserved.
+ * ---------------------------------------------------------------------- */
+static int or_nmobile(const or_rep *R) {
+    int c = 0;
+    for (int i = 0; i < R->n; ++i) c += (R->role[i] == 1);
+    return c;
+}
+
+static void or_nhc_masses(const or_rep *R, double *Q) {
+    double t2 = R->nhc_tau * R->nhc_tau;
+    for (int j = 0; j < R->nhc_len; ++j) Q[j] = (j == 0 ? (double)(R->dim * or_nmobile(R)) : 1.0) * R->kT * t2;
+}
+
+double or_nhc_energy(const or_rep *R) {
+    double Q[8], e = 0.0;
+    if (R->nhc_len <= 0) return 0.0;
+    or_nhc_masses(R, Q);
+    double nf = (double)(R->dim * or_nmobile(R));
+    for (int j = 0; j < R->nhc_len; ++j) {
+        e += 0.5 * Q[j] * R->nhc_v[j] * R->nhc_v[j];
+        e += (j == 0 ? nf : 1.0) * R->kT * R->nhc_xi[j];
+    }
+    return e;
+}
+
+static double or_nhc_force(const or_rep *R, const double *Q, double k2, double nf, int j) {
+    if (j == 0) return (k2 - nf * R->kT) / Q[0];
+    return (Q[j - 1] * R->nhc_v[j - 1] * R->nhc_v[j - 1] - R->kT) / Q[j];
+}
+
+static void or_nhc_half(or_rep *R, double h) {
+    int M = R->nhc_len, D = R->dim;
+    double Q[8], nf = (double)(D * or_nmobile(R)), k2 = 0.0;
+    double *v = R->nhc_v;
+    or_nhc_masses(R, Q);
+    for (int i = 0; i < R->n; ++i)
+        if (R->role[i] == 1)
+            for (int a = 0; a < D; ++a) k2 += R->v[3 * i + a] * R->v[3 * i + a];
+    v[M - 1] += 0.25 * h * or_nhc_force(R, Q, k2, nf, M - 1);
+    for (int j = M - 2; j >= 0; --j) {
+        double damp = exp(-0.125 * h * v[j + 1]);
+        v[j] *= damp;
+        v[j] += 0.25 * h * or_nhc_force(R, Q, k2, nf, j);
+        v[j] *= damp;
+    }
+    double s = exp(-0.5 * h * v[0]);
+    for (int i = 0; i < R->n; ++i)
+        if (R->role[i] == 1)
+            for (int a = 0; a < D; ++a) R->v[3 * i + a] *= s;
+    k2 *= s * s;
+    for (int j = 0; j < M; ++j) R->nhc_xi[j] += 0.5 * h * v[j];
+    for (int j = 0; j < M - 1; ++j) {
+        double damp = exp(-0.125 * h * v[j + 1]);
+        v[j] *= damp;
+        v[j] += 0.25 * h * or_nhc_force(R, Q, k2, nf, j);
+        v[j] *= damp;
+    }
+    v[M - 1] += 0.25 * h * or_nhc_force(R, Q, k2, nf, M - 1);
+}
+
 void or_run(or_rep *R, const or_params *P, int nsteps) {
     int n = R->n, nr = or_nrig(R), D = R->dim;
     double h = P->dt;
@@ -898,6 +969,7 @@ void or_run(or_rep *R, const or_params *P, int nsteps) {
     for (int it = 0; it < nsteps; ++it) {
         R->t_h += h * exp(R->dV / R->kT);
         R->t_md += h;
+        if (R->nhc_len > 0) or_nhc_half(R, h);            /* chain half step (instead of O) */
         /* B */
         for (int i = 0; i < n; ++i)
             if (R->role[i] == 1)
@@ -911,8 +983,8 @@ void or_run(or_rep *R, const or_params *P, int nsteps) {
             else if (R->role[i] == 2)
                 for (int a = 0; a < D; ++a) R->x[3 * i + a] += 0.5 * h * R->vbody[a];
         }
-        /* O */
-        for (int i = 0; i < n; ++i) {
+        /* O (Langevin only) */
+        for (int i = 0; i < n && R->nhc_len == 0; ++i) {
             if (R->role[i] != 1) continue;
             or_normals(P->seed, R->rep_id, R->step, i, 0, z);
             R->v[3 * i + 0] = c * R->v[3 * i + 0] + s * z[0];
@@ -956,6 +1028,7 @@ void or_run(or_rep *R, const or_params *P, int nsteps) {
         for (int i = 0; i < n; ++i)
             if (R->role[i] == 2)
                 for (int a = 0; a < 3; ++a) R->v[3 * i + a] = R->vbody[a];
+        if (R->nhc_len > 0) or_nhc_half(R, h);
         R->step += 1;
     }
     or_kinetic(R);

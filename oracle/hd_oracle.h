@@ -68,6 +68,13 @@ typedef struct {
     int nbond;
     const int *bonds;                 /* [nbond][2] */
     double kbond, rbond;
+    /* Nose-Hoover chain thermostat (Sec. 3.1.1) in place of Langevin when
+     * nhc_len > 0: chain length (<= 8), period tau of the thermostat masses
+     * Q_1 = N_f kT tau^2, Q_j = kT tau^2, positions xi and velocities v of
+     * the chain; it acts on the mobile atoms (N_f = dim n_mobile) */
+    int nhc_len;
+    double nhc_tau;
+    double nhc_xi[8], nhc_v[8];
 } or_rep;
 
 typedef struct {
@@ -105,6 +112,7 @@ double or_lowest_eig(const or_rep *R, const or_params *P, const double *x, doubl
 void   or_eig_grad(const or_rep *R, const or_params *P, const double *x, const double *v, double *g);
 void   or_dv2(const or_rep *R, double e, double out[2]);
 void   or_dv13(const or_rep *R, double dv1, double dv2, double out[3]);
+double or_nhc_energy(const or_rep *R);
 int    or_num_threads(void);
 
 #endif

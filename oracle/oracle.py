@@ -60,6 +60,7 @@ class OrRep(C.Structure):
         ("eig", C.c_double), ("dV1", C.c_double), ("dV2", C.c_double), ("dVe", C.c_double),
         ("vslide", C.c_double), ("slide_x0", C.c_double), ("slide_step0", C.c_int64),
         ("nbond", C.c_int), ("bonds", C.POINTER(C.c_int)), ("kbond", C.c_double), ("rbond", C.c_double),
+        ("nhc_len", C.c_int), ("nhc_tau", C.c_double), ("nhc_xi", C.c_double * 8), ("nhc_v", C.c_double * 8),
     ]
 
 
@@ -112,6 +113,8 @@ def lib():
         L.or_eig_grad.argtypes = [rp, pp, dp, dp, dp]
         L.or_dv2.argtypes = [rp, C.c_double, dp]
         L.or_dv13.argtypes = [rp, C.c_double, C.c_double, dp]
+        L.or_nhc_energy.argtypes = [rp]
+        L.or_nhc_energy.restype = C.c_double
         _lib = L
     return _lib
 
@@ -200,6 +203,11 @@ class OracleReplica:
         s.nbond = len(self.bonds)
         s.bonds = self.bonds.ctypes.data_as(C.POINTER(C.c_int))
         s.kbond, s.rbond = float(getattr(rep, "k_bond", 57.2)), float(getattr(rep, "r_bond", 1.12))
+        # Nose-Hoover chain in place of Langevin (0: Langevin)
+        s.nhc_len = int(getattr(rep, "nhc_len", 0))
+        s.nhc_tau = float(getattr(rep, "nhc_tau", 0.5))
+        if not 0 <= s.nhc_len <= 8:
+            raise ValueError("nhc_len must be in [0, 8]")
         self.s = s
         self.rep = rep
         if draw_velocities is None:
@@ -313,6 +321,10 @@ class OracleReplica:
         out = np.zeros(3)
         lib().or_dv13(C.byref(self.s), float(dv1), float(dv2), _dp(out))
         return out
+
+    def nhc_energy(self):
+        """The chain's part of the conserved extended energy."""
+        return lib().or_nhc_energy(C.byref(self.s))
 
     def transition(self, xq, theta=0.5):
         md = np.zeros(1)

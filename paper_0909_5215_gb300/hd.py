@@ -177,9 +177,11 @@ def make_params(params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, pre
 def make_descs(reps):
     """Build the C descriptors; returns (array, keep-alive list).  Replicas
     asking for what the library does not compute (the eigenvalue bias of
-    Eq. 13/15, continuous sliding, harmonic tip bonds of Eq. 12) are refused
-    rather than run without it."""
+    Eq. 13/15, continuous sliding, harmonic tip bonds of Eq. 12, the
+    Nose-Hoover chain) are refused rather than run without it."""
     for k, r in enumerate(reps):
+        if getattr(r, "nhc_len", 0):
+            raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: the Nose-Hoover chain is not implemented on the GPU" % k)
         if getattr(r, "eig_on", 0):
             raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: the eigenvalue bias is not implemented on the GPU" % k)
         if getattr(r, "v_slide", 0.0):

@@ -89,6 +89,10 @@ class Replica:
     bonds: np.ndarray | None = None
     k_bond: float = 57.2
     r_bond: float = 1.12
+    # Nose-Hoover chain (length nhc_len, period nhc_tau) in place of Langevin;
+    # 0: Langevin.  Evaluated by the CPU oracle only so far.
+    nhc_len: int = 0
+    nhc_tau: float = 0.5
 
     @property
     def n(self) -> int:

@@ -162,3 +162,13 @@ def test_tip_bonds_are_refused_not_dropped():
     with pytest.raises(hd.HdError) as ei:
         hd.make_descs([M.paper3d()])
     assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
+
+
+def test_nose_hoover_chain_is_refused_not_dropped():
+    from conftest import small2d
+    from paper_0909_5215_gb300 import hd
+    r = small2d()
+    r.nhc_len = 3
+    with pytest.raises(hd.HdError) as ei:
+        hd.make_descs([r])
+    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
