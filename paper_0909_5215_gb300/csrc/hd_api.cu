@@ -748,6 +748,10 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
         if (can_graph && c->persist_graph_ok) {
             auto it = c->graphs.find(n_steps);
             if (it == c->graphs.end()) {
+                if (c->graphs.size() >= 8) {  // keep at most 8 step counts, as on the per-phase path
+                    for (auto &gx : c->graphs) cudaGraphExecDestroy(gx.second);
+                    c->graphs.clear();
+                }
                 cudaGraph_t g = nullptr;
                 cudaGraphExec_t ge = nullptr;
                 bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
