@@ -804,7 +804,7 @@ void or_bias_eval(or_rep *R, const or_params *P) {
     double *ge = NULL;
     if (P->bias_on && R->eig_on) {
         double b2[2], c[3];
-        int maxit = R->eig_maxit > 0 ? R->eig_maxit : 100;
+        int maxit = R->eig_maxit > 0 ? R->eig_maxit : 3 * R->n;   /* to convergence: capped at the allowed dimension */
         R->eig = or_lowest_eig(R, P, R->x, R->veig, maxit, 1e-10);
         or_dv2(R, R->eig, b2);
         or_dv13(R, bv[0], b2[0], c);

@@ -191,7 +191,7 @@ class OracleReplica:
         # eigenvalue bias (Eq. 13, Eq. 15): off unless the replica asks for it
         self.veig = np.zeros((n, 3))
         s.eig_on = int(getattr(rep, "eig_on", 0))
-        s.eig_maxit = int(getattr(rep, "eig_maxit", 100))
+        s.eig_maxit = int(getattr(rep, "eig_maxit", 2000))
         s.eig_lo, s.eig_hi = float(getattr(rep, "eig_lo", 0.0)), float(getattr(rep, "eig_hi", 1.0))
         s.veig = _dp(self.veig)
         # continuous sliding: slider x = x_S0 + k (v dt) after the k-th step from here

@@ -79,7 +79,7 @@ class Replica:
     eig_on: int = 0
     eig_lo: float = 0.0
     eig_hi: float = 1.0
-    eig_maxit: int = 100
+    eig_maxit: int = 2000          # Lanczos steps per evaluation, at most (capped at the allowed dimension)
     # continuous sliding (slider moving at v_slide along x every step);
     # evaluated by the CPU oracle only so far
     v_slide: float = 0.0
