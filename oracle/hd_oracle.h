@@ -23,6 +23,11 @@
  *     FIRE quenches to the basin minimum r_O (after Eq. 7) and a transition
  *     test by displacement from r_O (Sec. 2.3).
  *
+ * Pins (tests/test_oracle_*.py) tie each function to closed forms, finite
+ * differences, brute force or invariants.  One quantity has no pin against
+ * the paper: time averages of F_R (Eq. 10), parity unpinned; the paper prints
+ * no value for them, so they are checked GPU against oracle only.
+ *
  * Every array is caller-owned.  Positions are [n][3] (z = 0 in 2-D) and are
  * never wrapped into the periodic box; minimum images are taken where two
  * positions are differenced.
