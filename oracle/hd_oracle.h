@@ -19,9 +19,11 @@
  *     Eq. 12 (the 3-D model of Sec. 3.2.1);
  *   - the rigid top layer pulled by the slider spring and the normal load
  *     (Sec. 3.1.1, Sec. 3.2.1), lateral force F_R = k (x_S - x_T), Eq. 10;
- *   - Langevin BAOAB dynamics with Philox4x32-10 noise, steepest-descent and
- *     FIRE quenches to the basin minimum r_O (after Eq. 7) and a transition
- *     test by displacement from r_O (Sec. 2.3).
+ *   - Langevin BAOAB dynamics with Philox4x32-10 noise, or a Nose-Hoover
+ *     chain (Sec. 3.1.1); the slider held still (stepped sliding) or moving
+ *     at a set velocity (continuous sliding, Sec. 3.1.1);
+ *   - steepest-descent and FIRE quenches to the basin minimum r_O (after
+ *     Eq. 7) and a transition test by displacement from r_O (Sec. 2.3).
  *
  * Pins (tests/test_oracle_*.py) tie each function to closed forms, finite
  * differences, brute force or invariants.  One quantity has no pin against
