@@ -212,7 +212,7 @@ static int or_cmp_int(const void *a, const void *b) {
 
 /* Same list through a cell grid (cells at least rl wide), then each row sorted. */
 static int or_list_cells(const or_rep *R, const double *x, double rl, int *nnb, int *nbr) {
-    int n = R->n, nc[3];
+    int n = R->n, nc[3], bad = 0;
     double lo[3], w[3];
     for (int a = 0; a < 3; ++a) {
         if (R->periodic[a]) {
@@ -220,6 +220,7 @@ static int or_list_cells(const or_rep *R, const double *x, double rl, int *nnb, 
             if (nc[a] < 3) nc[a] = 1;
             lo[a] = 0.0;
             w[a] = R->L[a] / nc[a];
+            for (int i = 0; i < n; ++i) bad |= !isfinite(x[3 * i + a]);
         } else {
             double mn = x[a], mx = x[a];
             for (int i = 1; i < n; ++i) {
@@ -228,8 +229,17 @@ static int or_list_cells(const or_rep *R, const double *x, double rl, int *nnb, 
             }
             lo[a] = mn;
             w[a] = rl * (1.0 + 1e-12);
-            nc[a] = (int)floor((mx - mn) / w[a]) + 1;
+            double span = (mx - mn) / w[a];
+            if (!(span < 65536.0)) { bad = 1; span = 0.0; }
+            nc[a] = (int)floor(span) + 1;
         }
+    }
+    /* a runaway configuration (a diverged quench: non-finite or wildly
+     * spread coordinates) gets empty rows and -1, instead of an unbounded
+     * cell grid */
+    if (bad) {
+        for (int i = 0; i < n; ++i) nnb[i] = 0;
+        return -1;
     }
     long ncell = (long)nc[0] * nc[1] * nc[2];
     int *cid = malloc(sizeof(int) * n), *start = calloc(ncell + 1, sizeof(int)), *list = malloc(sizeof(int) * n);
@@ -298,6 +308,7 @@ int or_nlist_brute(or_rep *R, double rl) {
 
 int or_nlist_cells(or_rep *R, double rl) {
     int over = or_list_cells(R, R->x, rl, R->nnb, R->nbr);
+    if (over < 0) over = R->n;                /* runaway positions: no usable list */
     memcpy(R->xb, R->x, sizeof(double) * 3 * R->n);
     R->nb_overflow += over;
     return over;
@@ -1087,11 +1098,11 @@ int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_it
     double rl = P->rc + P->skin, half_skin2 = 0.25 * P->skin * P->skin;
     memcpy(xq, R->x, sizeof(double) * 3 * n);
     memcpy(xb, xq, sizeof(double) * 3 * n);
-    or_list_cells(R, xq, rl, nnb, nbr);
+    int listed = or_list_cells(R, xq, rl, nnb, nbr) >= 0;
     /* FIRE state */
     double dt = step_size, dtmax = 10.0 * step_size, alpha = 0.1;
     int npos = 0, it;
-    for (it = 0; it < max_iter; ++it) {
+    for (it = 0; listed && it < max_iter; ++it) {
         double mx = 0.0;
         for (int i = 0; i < n; ++i) {
             double dd = 0.0;
@@ -1099,11 +1110,12 @@ int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_it
             if (dd > mx) mx = dd;
         }
         if (mx > half_skin2) {
-            or_list_cells(R, xq, rl, nnb, nbr);
+            if (or_list_cells(R, xq, rl, nnb, nbr) < 0) { fmax = NAN; break; }
             memcpy(xb, xq, sizeof(double) * 3 * n);
         }
         or_qforce(R, P, xq, nnb, nbr, f, fb, &fmax);
         if (fmax < ftol) break;
+        if (!(fmax < 1e30)) break;            /* diverged (step too large for the stiffest mode) */
         if (method == 0) {
             for (int i = 0; i < n; ++i) {
                 if (R->role[i] == 1)
@@ -1161,6 +1173,7 @@ int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_it
             }
         }
     }
+    if (!listed) fmax = NAN;
     if (fmax_out) *fmax_out = fmax;
     free(v); free(f); free(xb); free(nbr); free(nnb);
     return it;
