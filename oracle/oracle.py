@@ -352,3 +352,23 @@ def run_batch(reps, nsteps):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def quench_batch(reps, method=1, ftol=1e-6, max_iter=20000, step_size=None):
+    """Quench a list of OracleReplica in parallel (OpenMP over replicas);
+    returns the quenched positions, iteration counts and final max forces."""
+    if step_size is None:
+        step_size = (0.002 if method == 0 else 0.01)
+    n = len(reps)
+    if n == 0:
+        return [], np.zeros(0, np.int32), np.zeros(0)
+    arr = (OrRep * n)()
+    for i, r in enumerate(reps):
+        arr[i] = r.s
+    xq = [np.zeros((r.n, 3)) for r in reps]
+    ptrs = (C.POINTER(C.c_double) * n)(*[_dp(x) for x in xq])
+    fmax = np.zeros(n)
+    iters = np.zeros(n, np.int32)
+    lib().or_quench_batch(arr, n, C.byref(reps[0].P), int(method), float(ftol), int(max_iter), float(step_size),
+                          ptrs, _dp(fmax), iters.ctypes.data_as(C.POINTER(C.c_int)))
+    return xq, iters, fmax

@@ -25,7 +25,26 @@ r_O.  A transition is dated at the boosted clock of the check that flags it
 (resolution: one check interval) and counts when the replica's period was
 still open at the previous check.  Periods that end inside a check interval
 are cut at dtau for the time accounting and for the boost-weighted average
-of F_R over the period, sampled at the checks (F_R times the t_h increment).
+of F_R over the period, sampled every `sample_every` steps (F_R times the
+t_h increment).
+
+The bias of Eq. 5 and Eq. 14 is measured from r_O, the minimum of the basin
+the replica is in (after Eq. 7).  That minimum moves with the slider, so by
+default every interval starts with a quench of each replica at its own slider
+position that sets r_O (requench).  A replica whose quench already lands more
+than theta from the carried r_O has lost its basin at that position: it makes
+its transition at the start of its period.  With `band`, each replica also
+runs an unbiased pre-run at its position and takes sigma_L and sigma_U as
+quantiles of the slopes sampled there (the pre-simulation of Sec. 3.1.2); the
+pre-run is ordinary MD and counts toward the period.
+
+ContinuousSliding runs the reference method the stepped scheme replaces: the
+slider moves at v_S every step (Sec. 3.1.1, method 1), F_R is averaged over
+bins of slider travel dx, and the same quench test dates transitions.
+slip_forces reads, from either log, the lateral force at each transition as
+the largest period average of F_R at the end of the stick phase that ends
+with it (the quantity the paper compares across methods, Sec. 3.1.2 and
+Fig. 9).
 """
 from __future__ import annotations
 
@@ -33,7 +52,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-OBS_T_H, OBS_DV, OBS_FR = 2, 5, 8       # columns of the OBS record
+OBS_STEP, OBS_T_H, OBS_DV, OBS_SIGMA, OBS_FR = 0, 2, 5, 6, 8     # columns of the OBS record
 
 
 @dataclass
@@ -60,19 +79,27 @@ class SteppedSliding:
     state: a model.Replica at the current slider position with r_O
     (pos_ref) set to its current basin minimum and, for hyperdynamics, its
     bias band set.  dx: slider step dx_S; v_s: sliding velocity (dtau = dx /
-    v_s); n_par: positions run at the same time.
+    v_s); n_par: positions run at the same time.  requench: set r_O at each
+    replica's own slider position when an interval starts.  band: None (keep
+    the state's bias band) or a dict with prerun (MD steps), sample_every,
+    q_lo, q_hi (quantiles of sigma for sigma_L, sigma_U), dvmax and m.
+    sample_every: MD steps between F_R samples (a divisor of check_every).
     """
 
     def __init__(self, state, params, dx, v_s, n_par, check_every=500, theta=0.5,
-                 quench=None, make_batch=None, max_checks=100000, rep_id0=1000):
-        if dx <= 0 or v_s <= 0 or n_par < 1 or check_every < 1:
-            raise ValueError("dx, v_s, n_par and check_every must be positive")
+                 quench=None, make_batch=None, max_checks=100000, rep_id0=1000,
+                 requench=True, band=None, sample_every=None):
+        sample_every = check_every if sample_every is None else sample_every
+        if dx <= 0 or v_s <= 0 or n_par < 1 or check_every < 1 or sample_every < 1 or check_every % sample_every:
+            raise ValueError("dx, v_s, n_par, check_every and sample_every must be positive, "
+                             "check_every a multiple of sample_every")
         self.state = state.copy()
         self.params = params
         self.dx = float(dx)
         self.dtau = float(dx) / float(v_s)
         self.n_par = int(n_par)
         self.check_every = int(check_every)
+        self.sample_every = int(sample_every)
         self.theta = float(theta)
         self.quench = dict(method=1, ftol=1e-4, max_iter=2000) if quench is None else dict(quench)
         if make_batch is None:
@@ -80,6 +107,13 @@ class SteppedSliding:
             make_batch = hd.Batch
         self.make_batch = make_batch
         self.max_checks = int(max_checks)
+        self.requench = bool(requench)
+        self.band = None
+        if band is not None:
+            self.band = dict(prerun=2000, sample_every=20, q_lo=0.05, q_hi=0.5, dvmax=4.0 * state.kT, m=2)
+            self.band.update(band)
+            if not (0.0 <= self.band["q_lo"] < self.band["q_hi"] <= 1.0) or self.band["prerun"] < self.band["sample_every"]:
+                raise ValueError("band: need 0 <= q_lo < q_hi <= 1 and prerun >= sample_every")
         self.x0 = np.array(state.slider, dtype=np.float64).copy()
         self.m = 0            # slider steps taken
         self.t_in = 0.0       # boosted time already spent at the current position
@@ -105,8 +139,12 @@ class SteppedSliding:
         """Run one parallel interval; returns the first slider index with a
         transition in it, or None."""
         R = self.n_par
+        if self.t_in >= self.dtau:          # a transition closed the current position's period
+            self.m += 1
+            self.t_in = 0.0
+            self.state.slider = self.slider_at(self.m)
         budget = np.full(R, self.dtau)
-        budget[0] = max(self.dtau - self.t_in, 0.0)
+        budget[0] = self.dtau - self.t_in
         reps = self._replicas()
         b = self.make_batch(reps, self.params)
         try:
@@ -115,29 +153,53 @@ class SteppedSliding:
             fr_sum, t_sum = np.zeros(R), np.zeros(R)
             snap = {}
             kstar = None
-            for _ in range(self.max_checks):
-                b.step(self.check_every)
-                self.log.md_steps += self.check_every
-                ob = np.asarray(b.obs())
-                th = ob[:, OBS_T_H]
+            if self.requench:
+                flags = np.asarray(b.quench(theta=self.theta, adopt=2, **self.quench))
+                for k in np.nonzero(flags)[0]:
+                    t_tr[k] = 0.0
+                    snap[int(k)] = (b.positions(k), b.velocities(k), b.qpos(k))
+
+            def settle(th):
+                # the first position with a transition, the positions before it,
+                # and whether all of those have used up their periods
+                hit = np.nonzero(np.isfinite(t_tr))[0]
+                ks = int(hit[0]) if hit.size else None
+                up = ks if ks is not None else R
+                return ks, up, all(th[k] >= budget[k] for k in range(up))
+
+            t_acc = np.zeros(R)                # boosted clock at the last F_R sample
+
+            def accumulate(ob):
                 # boost-weighted F_R over each open period, cut at its end
-                dt = np.clip(np.minimum(th, budget) - np.minimum(t_prev, budget), 0.0, None)
+                nonlocal t_acc
+                th = ob[:, OBS_T_H]
+                dt = np.clip(np.minimum(th, budget) - np.minimum(t_acc, budget), 0.0, None)
                 dt[np.isfinite(t_tr)] = 0.0
-                fr_sum += ob[:, OBS_FR] * dt
-                t_sum += dt
+                fr_sum[:] += ob[:, OBS_FR] * dt
+                t_sum[:] += dt
+                t_acc = th.copy()
+
+            kstar, upto, done = settle(t_prev)
+            if self.band is not None and not done:
+                self._prerun(b, R, accumulate)
+            checks = 0
+            while not done:
+                if checks == self.max_checks:
+                    raise RuntimeError("interval did not finish within max_checks quench checks")
+                checks += 1
+                for _ in range(self.check_every // self.sample_every):
+                    b.step(self.sample_every)
+                    self.log.md_steps += self.sample_every
+                    ob = np.asarray(b.obs())
+                    accumulate(ob)
+                th = ob[:, OBS_T_H]
                 flags = np.asarray(b.quench(theta=self.theta, adopt=0, **self.quench))
                 for k in range(R):
                     if flags[k] and not np.isfinite(t_tr[k]) and t_prev[k] < budget[k]:
                         t_tr[k] = min(th[k], budget[k])
                         snap[k] = (b.positions(k), b.velocities(k), b.qpos(k))
                 t_prev = th.copy()
-                hit = np.nonzero(np.isfinite(t_tr))[0]
-                kstar = int(hit[0]) if hit.size else None
-                upto = kstar if kstar is not None else R
-                if all(th[k] >= budget[k] for k in range(upto)):
-                    break
-            else:
-                raise RuntimeError("interval did not finish within max_checks quench checks")
+                kstar, upto, done = settle(th)
             # accept periods [0, upto) in full and, with a transition, the
             # transition's period up to the transition
             for k in range(upto):
@@ -162,6 +224,24 @@ class SteppedSliding:
         finally:
             b.close()
 
+    def _prerun(self, b, R, accumulate):
+        """Unbiased MD at every position, then sigma_L, sigma_U per replica
+        from the slopes sampled during it (Eq. 14's band)."""
+        B = self.band
+        m = float(B["m"])
+        b.set_bias(np.tile([0.0, 0.0, 1.0, m], (R, 1)))
+        n = int(B["prerun"]) // int(B["sample_every"])
+        sig = np.empty((n, R))
+        for i in range(n):
+            b.step(int(B["sample_every"]))
+            ob = np.asarray(b.obs())
+            accumulate(ob)
+            sig[i] = ob[:, OBS_SIGMA]
+        self.log.md_steps += n * int(B["sample_every"])
+        lo, hi = np.quantile(sig, B["q_lo"], axis=0), np.quantile(sig, B["q_hi"], axis=0)
+        hi = np.maximum(hi, lo + 1e-12 * np.maximum(1.0, np.abs(lo)))
+        b.set_bias(np.column_stack([np.full(R, float(B["dvmax"])), lo, hi, np.full(R, m)]))
+
     def _period(self, k, t, fr_sum, t_sum, transition):
         self.log.periods.append(Period(index=self.m + k, slider_x=float(self.slider_at(self.m + k)[0]), time=float(t),
                                        fr_mean=float(fr_sum / t_sum) if t_sum > 0 else float("nan"),
@@ -173,3 +253,110 @@ class SteppedSliding:
         while self.m < target:
             self.interval()
         return self.log
+
+
+class ContinuousSliding:
+    """Continuous sliding (Sec. 3.1.1, method 1) of n_samples independent
+    replicas: the slider's x moves by v_s dt every MD step.
+
+    state: a model.Replica with r_O (pos_ref) set to its basin minimum.
+    Every `sample_every` steps F_R is read and added to the bin of slider
+    travel dx it falls in; every `check_every` steps a quench (adopt = 1)
+    flags the replicas that left their basin and moves their r_O to the new
+    minimum.  The bias stays off: with the slider moving there is no frozen
+    potential to boost.  The batch must support moving sliders (the replica
+    field v_slide).
+    """
+
+    def __init__(self, state, params, v_s, n_samples, dx, sample_every=100, check_every=500, theta=0.5,
+                 quench=None, make_batch=None, rep_id0=2000):
+        if v_s <= 0 or n_samples < 1 or dx <= 0 or sample_every < 1 or check_every % sample_every:
+            raise ValueError("v_s, n_samples, dx, sample_every must be positive; check_every a multiple of sample_every")
+        if getattr(params, "bias_on", 0):
+            raise ValueError("continuous sliding runs unbiased (bias_on = 0)")
+        self.state = state.copy()
+        self.params = params
+        self.v_s, self.dx = float(v_s), float(dx)
+        self.n_samples = int(n_samples)
+        self.sample_every, self.check_every = int(sample_every), int(check_every)
+        self.theta = float(theta)
+        self.quench = dict(method=1, ftol=1e-4, max_iter=2000) if quench is None else dict(quench)
+        if make_batch is None:
+            from . import hd
+            make_batch = hd.Batch
+        self.make_batch = make_batch
+        self.rep_id0 = int(rep_id0)
+        self.x0 = float(state.slider[0])
+
+    def run(self, distance):
+        """Slide every sample by `distance`; returns one SlidingLog per sample
+        with a Period per bin of slider travel dx."""
+        dt = float(self.params.dt)
+        nsteps = int(np.ceil(float(distance) / (self.v_s * dt) / self.sample_every)) * self.sample_every
+        reps = []
+        for k in range(self.n_samples):
+            r = self.state.copy()
+            r.rep_id = self.rep_id0 + k
+            r.t_h0, r.t_md0, r.step0 = 0.0, 0.0, 0
+            r.v_slide = self.v_s
+            reps.append(r)
+        nbin = int(np.ceil(float(distance) / self.dx)) + 1
+        fr_sum = np.zeros((self.n_samples, nbin))
+        cnt = np.zeros((self.n_samples, nbin))
+        trans = [[] for _ in range(self.n_samples)]
+        b = self.make_batch(reps, self.params)
+        try:
+            for done in range(self.sample_every, nsteps + 1, self.sample_every):
+                b.step(self.sample_every)
+                ob = np.asarray(b.obs())
+                travel = self.v_s * dt * ob[:, OBS_STEP]
+                j = np.minimum((travel / self.dx).astype(np.int64), nbin - 1)
+                idx = np.arange(self.n_samples)
+                fr_sum[idx, j] += ob[:, OBS_FR]
+                cnt[idx, j] += 1
+                if done % self.check_every == 0:
+                    flags = np.asarray(b.quench(theta=self.theta, adopt=1, **self.quench))
+                    for k in np.nonzero(flags)[0]:
+                        trans[k].append((int(j[k]), self.x0 + float(travel[k]), float(ob[k, 1])))
+        finally:
+            b.close()
+        logs = []
+        tbin = self.dx / self.v_s
+        for k in range(self.n_samples):
+            lg = SlidingLog(md_steps=nsteps, intervals=1)
+            hit = {t[0] for t in trans[k]}
+            for i in range(nbin):
+                if cnt[k, i] == 0:
+                    continue
+                lg.periods.append(Period(index=i, slider_x=self.x0 + i * self.dx, time=tbin,
+                                         fr_mean=float(fr_sum[k, i] / cnt[k, i]), transition=i in hit))
+            lg.transitions = trans[k]
+            logs.append(lg)
+        return logs
+
+
+def slip_forces(log, min_gap=1, window=None):
+    """The lateral force at each transition of a SlidingLog: the largest
+    period average of F_R over the stick phase that the transition ends, or
+    over its last `window` periods (the transition's own included), which
+    keeps the relaxation right after the previous slip out.  Transitions
+    fewer than min_gap slider positions after the previous one belong to
+    the same slip (a slip in several hops) and end no new stick phase.
+    Returns [(index of the transition, force)]."""
+    out = []
+    last = None
+    cur = []
+    for p in log.periods:
+        cur.append(p.fr_mean)
+        if not p.transition:
+            continue
+        if last is not None and p.index - last < min_gap:
+            last = p.index
+            cur = []
+            continue
+        vals = [v for v in (cur if window is None else cur[-int(window):]) if np.isfinite(v)]
+        if vals:
+            out.append((p.index, float(max(vals))))
+        last = p.index
+        cur = []
+    return out

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from conftest import small2d
+from oracle_batch import OracleBatch
 
 DT = 0.005
 OBS_LEN = 24
@@ -18,23 +19,31 @@ OBS_LEN = 24
 
 class ScriptedBatch:
     """Replica at slider index j: t_h grows by alpha[j] dt per MD step, a
-    transition is flagged once t_h >= T[j], F_R reads fr[j]."""
+    transition is flagged once t_h >= T[j], F_R reads fr[j], the slope sigma
+    reads 10 j + (MD steps so far) / 1000; set_bias calls are recorded."""
 
     def __init__(self, reps, params, x0, dx, alpha, T, fr):
         self.idx = [int(round((r.slider[0] - x0) / dx)) for r in reps]
         self.n = [r.n for r in reps]
         self.th = np.zeros(len(reps))
+        self.steps = 0
         self.alpha, self.T, self.fr = alpha, T, fr
+        self.bias = []
         self.closed = False
 
     def step(self, n):
         self.th += n * DT * np.array([self.alpha.get(j, 1.0) for j in self.idx])
+        self.steps += n
 
     def obs(self):
         ob = np.zeros((len(self.idx), OBS_LEN))
         ob[:, 2] = self.th
+        ob[:, 6] = [10.0 * j + self.steps / 1000.0 for j in self.idx]
         ob[:, 8] = [self.fr.get(j, 0.0) for j in self.idx]
         return ob
+
+    def set_bias(self, bias):
+        self.bias.append(np.asarray(bias, dtype=np.float64).reshape(len(self.idx), 4).copy())
 
     def quench(self, theta=0.5, adopt=0, **kw):
         return np.array([int(self.th[k] >= self.T.get(j, np.inf)) for k, j in enumerate(self.idx)], dtype=np.int32)
@@ -58,7 +67,7 @@ class ScriptedBatch:
         self.closed = True
 
 
-def _driver(alpha=None, T=None, fr=None, n_par=4, dtau=1.0, check_every=50):
+def _driver(alpha=None, T=None, fr=None, n_par=4, dtau=1.0, check_every=50, **kw):
     from paper_0909_5215_gb300 import model as M
     from paper_0909_5215_gb300.sliding import SteppedSliding
     st = small2d()
@@ -73,7 +82,7 @@ def _driver(alpha=None, T=None, fr=None, n_par=4, dtau=1.0, check_every=50):
         return b
 
     d = SteppedSliding(st, M.Params(prec=1), dx=dx, v_s=dx / dtau, n_par=n_par, check_every=check_every,
-                       make_batch=mk)
+                       make_batch=mk, **kw)
     return d, made
 
 
@@ -128,45 +137,149 @@ def test_boosted_clock_and_f_r_average():
         _driver(n_par=0)
 
 
-class OracleBatch:
-    """The batch calls on the CPU oracle (test infrastructure only)."""
+def test_basin_lost_at_a_position_is_a_transition_at_its_start():
+    # the quench that sets r_O at each position already leaves the basin at
+    # index 2: a transition at time 0 of that period
+    d, _ = _driver(T={2: 0.0, 3: 0.0})
+    assert d.interval() == 2
+    assert [p.index for p in d.log.periods] == [0, 1, 2]
+    assert d.log.periods[2].transition and d.log.periods[2].time == 0.0
+    assert d.time == pytest.approx(2.0) and d.t_in == 0.0
+    # without the requench the first check finds it, a check interval later
+    d, _ = _driver(T={2: 0.0, 3: 0.0}, requench=False)
+    assert d.interval() == 2
+    assert d.log.periods[2].time == pytest.approx(0.25)
 
-    def __init__(self, reps, params, oracle_mod):
-        self.o = [oracle_mod.OracleReplica(r, params) for r in reps]
-        self.xq = [o.x.copy() for o in self.o]
+
+def test_transition_that_closes_a_period_moves_to_the_next_position():
+    # flagged at the check where index 0's period ends (t_h = 1.0)
+    d, _ = _driver(T={0: 1.0}, n_par=2)
+    assert d.interval() == 0
+    assert d.t_in == pytest.approx(1.0)
+    d.interval()
+    # no empty period at index 0: the next interval starts at index 1
+    assert [p.index for p in d.log.periods] == [0, 1, 2]
+    assert all(p.time > 0 for p in d.log.periods)
+
+
+def test_band_prerun_sets_each_replica_band_from_its_own_slopes():
+    band = dict(prerun=200, sample_every=50, q_lo=0.25, q_hi=0.75, dvmax=0.3, m=3)
+    d, made = _driver(n_par=3, band=band)
+    d.interval()
+    b = made[0]
+    assert len(b.bias) == 2
+    assert np.all(b.bias[0][:, 0] == 0.0)                 # the pre-run is unbiased
+    # slopes sampled after 50, 100, 150, 200 steps: 10 j + {0.05 .. 0.2}
+    samples = np.array([0.05, 0.1, 0.15, 0.2])
+    for j in range(3):
+        dvmax, lo, hi, m = b.bias[1][j]
+        assert (dvmax, m) == (0.3, 3.0)
+        assert lo == pytest.approx(10 * j + np.quantile(samples, 0.25))
+        assert hi == pytest.approx(10 * j + np.quantile(samples, 0.75))
+    # the pre-run is MD at the position and counts toward the period: it
+    # fills the 200-step periods, and one check follows it
+    assert d.log.md_steps == 200 + 50
+    assert d.time == pytest.approx(3.0)
+    with pytest.raises(ValueError):
+        _driver(band=dict(q_lo=0.6, q_hi=0.5))
+
+
+def test_f_r_is_sampled_between_checks():
+    # F_R changes only through which replica is read; sampling every 10 steps
+    # gives the same boosted average as sampling at the checks
+    d, _ = _driver(alpha={0: 4.0, 1: 1.0}, fr={0: 0.3, 1: 0.5}, n_par=2, sample_every=10)
+    d.interval()
+    assert [p.fr_mean for p in d.log.periods] == [pytest.approx(0.3), pytest.approx(0.5)]
+    with pytest.raises(ValueError):
+        _driver(sample_every=30)
+
+
+def _log(rows):
+    from paper_0909_5215_gb300.sliding import Period, SlidingLog
+    lg = SlidingLog()
+    for i, f, t in rows:
+        lg.periods.append(Period(index=i, slider_x=0.1 * i, time=1.0, fr_mean=f, transition=t))
+    return lg
+
+
+def test_slip_forces_stick_phases_windows_and_hops():
+    from paper_0909_5215_gb300.sliding import slip_forces
+    rows = [(0, 1.0, False), (1, 3.0, False), (2, 2.0, False), (3, 2.5, True),    # slip at 3, peak 3.0
+            (3, 9.0, False), (4, 1.0, False), (5, 1.5, False), (6, 2.0, True),    # peak 9.0 right after the slip
+            (7, 0.5, True),                                                      # second hop of the same slip
+            (8, 1.0, False), (9, float("nan"), True)]                            # nan periods are skipped
+    lg = _log(rows)
+    assert slip_forces(lg) == [(3, 3.0), (6, 9.0), (7, 0.5), (9, 1.0)]
+    assert slip_forces(lg, min_gap=2) == [(3, 3.0), (6, 9.0), (9, 1.0)]
+    # the last 3 periods only: the relaxation after the previous slip drops out
+    assert slip_forces(lg, min_gap=2, window=3) == [(3, 3.0), (6, 2.0), (9, 1.0)]
+
+
+class ScriptedSlider:
+    """Moving-slider batch: F_R = 2 x travel; a replica flags a transition
+    at the first check after its slider has travelled past each of `slips`."""
+
+    def __init__(self, reps, params, slips):
+        self.v = [r.v_slide for r in reps]
+        self.dt = params.dt
+        self.steps = 0
+        self.slips = slips
+        self.done = [set() for _ in reps]
+        self.adopts = []
 
     def step(self, n):
-        for o in self.o:
-            o.run(n)
+        self.steps += n
 
     def obs(self):
-        ob = np.zeros((len(self.o), OBS_LEN))
-        for k, o in enumerate(self.o):
-            ob[k, 2], ob[k, 5], ob[k, 8] = o.s.t_h, o.s.dV, o.s.FR
+        ob = np.zeros((len(self.v), OBS_LEN))
+        ob[:, 0] = self.steps
+        ob[:, 1] = self.steps * self.dt
+        ob[:, 8] = [2.0 * v * self.dt * self.steps for v in self.v]
         return ob
 
-    def quench(self, method=1, ftol=1e-4, max_iter=2000, theta=0.5, adopt=0, step_size=None):
-        flags = []
-        for k, o in enumerate(self.o):
-            xq, _, _ = o.quench(method=method, ftol=ftol, max_iter=max_iter)
-            self.xq[k] = xq
-            flags.append(int(o.transition(xq, theta)[0]))
-        return np.array(flags, dtype=np.int32)
-
-    def positions(self, k):
-        return self.o[k].x.copy()
-
-    def velocities(self, k):
-        return self.o[k].v.copy()
-
-    def qpos(self, k):
-        return self.xq[k].copy()
-
-    def ref(self, k):
-        return self.o[k].xo.copy()
+    def quench(self, theta=0.5, adopt=0, **kw):
+        self.adopts.append(adopt)
+        out = []
+        for k, v in enumerate(self.v):
+            hit = [x for x in self.slips if v * self.dt * self.steps >= x and x not in self.done[k]]
+            self.done[k].update(hit)
+            out.append(int(bool(hit)))
+        return np.array(out, dtype=np.int32)
 
     def close(self):
         pass
+
+
+def test_continuous_sliding_bins_and_dates_transitions():
+    from paper_0909_5215_gb300 import model as M
+    from paper_0909_5215_gb300.sliding import ContinuousSliding, slip_forces
+    st = small2d()
+    p = M.Params(prec=1, dt=0.005)
+    made = []
+
+    def mk(reps, params):
+        b = ScriptedSlider(reps, params, slips=[0.53, 1.01])
+        made.append(b)
+        return b
+
+    # bins of 0.1003 sigma: no sample falls on a bin edge
+    cs = ContinuousSliding(st, p, v_s=0.01, n_samples=2, dx=0.1003, sample_every=100, check_every=400,
+                           make_batch=mk)
+    logs = cs.run(1.2)
+    b = made[0]
+    assert all(v == 0.01 for v in b.v) and set(b.adopts) == {1}
+    for lg in logs:
+        assert lg.md_steps == 24000
+        # a sample every 0.005 sigma of travel; bin i holds travel in [0.1003 i, 0.1003 (i + 1))
+        assert [q.index for q in lg.periods] == list(range(12))
+        assert lg.periods[0].fr_mean == pytest.approx(2.0 * np.mean(np.arange(1, 21) * 0.005))
+        assert all(q.time == pytest.approx(10.03) for q in lg.periods)
+        # checks every 0.02 of travel: the slips are dated at 0.54 and 1.02
+        assert [t[0] for t in lg.transitions] == [5, 10]
+        assert [t[1] - st.slider[0] for t in lg.transitions] == [pytest.approx(0.54), pytest.approx(1.02)]
+        assert [i for i, _ in slip_forces(lg)] == [5, 10]
+    with pytest.raises(ValueError):
+        ContinuousSliding(st, M.Params(prec=1, bias_on=1), v_s=0.01, n_samples=1, dx=0.1, make_batch=mk)
 
 
 def test_oracle_backed_sliding_through_a_slip(oracle_mod):
