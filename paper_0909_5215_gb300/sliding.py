@@ -16,6 +16,11 @@ the first one in slider order: only it is reached by the serial sequence of
 periods.)  Without a transition all n_par periods are accepted and the next
 interval starts at x_{m+n_par} from the state of the last replica.
 
+run_intervals and run_ensemble advance several independent runs (samples
+with their own states and replica ids) together, one batch per interval
+holding every sample's replicas; each sample's result is that of its own
+run.
+
 The driver is host logic over a batch object with the calls of hd.Batch
 (step, obs, quench, positions, velocities, qpos, ref, close); make_batch
 builds one from replicas and parameters (hd.Batch by default).  Transitions
@@ -138,109 +143,12 @@ class SteppedSliding:
     def interval(self):
         """Run one parallel interval; returns the first slider index with a
         transition in it, or None."""
-        R = self.n_par
-        if self.t_in >= self.dtau:          # a transition closed the current position's period
-            self.m += 1
-            self.t_in = 0.0
-            self.state.slider = self.slider_at(self.m)
-        budget = np.full(R, self.dtau)
-        budget[0] = self.dtau - self.t_in
-        reps = self._replicas()
-        b = self.make_batch(reps, self.params)
-        try:
-            t_prev = np.zeros(R)
-            t_tr = np.full(R, np.inf)          # boosted time of a counted transition
-            fr_sum, t_sum = np.zeros(R), np.zeros(R)
-            snap = {}
-            kstar = None
-            if self.requench:
-                flags = np.asarray(b.quench(theta=self.theta, adopt=2, **self.quench))
-                for k in np.nonzero(flags)[0]:
-                    t_tr[k] = 0.0
-                    snap[int(k)] = (b.positions(k), b.velocities(k), b.qpos(k))
+        return run_intervals([self])[0]
 
-            def settle(th):
-                # the first position with a transition, the positions before it,
-                # and whether all of those have used up their periods
-                hit = np.nonzero(np.isfinite(t_tr))[0]
-                ks = int(hit[0]) if hit.size else None
-                up = ks if ks is not None else R
-                return ks, up, all(th[k] >= budget[k] for k in range(up))
-
-            t_acc = np.zeros(R)                # boosted clock at the last F_R sample
-
-            def accumulate(ob):
-                # boost-weighted F_R over each open period, cut at its end
-                nonlocal t_acc
-                th = ob[:, OBS_T_H]
-                dt = np.clip(np.minimum(th, budget) - np.minimum(t_acc, budget), 0.0, None)
-                dt[np.isfinite(t_tr)] = 0.0
-                fr_sum[:] += ob[:, OBS_FR] * dt
-                t_sum[:] += dt
-                t_acc = th.copy()
-
-            kstar, upto, done = settle(t_prev)
-            if self.band is not None and not done:
-                self._prerun(b, R, accumulate)
-            checks = 0
-            while not done:
-                if checks == self.max_checks:
-                    raise RuntimeError("interval did not finish within max_checks quench checks")
-                checks += 1
-                for _ in range(self.check_every // self.sample_every):
-                    b.step(self.sample_every)
-                    self.log.md_steps += self.sample_every
-                    ob = np.asarray(b.obs())
-                    accumulate(ob)
-                th = ob[:, OBS_T_H]
-                flags = np.asarray(b.quench(theta=self.theta, adopt=0, **self.quench))
-                for k in range(R):
-                    if flags[k] and not np.isfinite(t_tr[k]) and t_prev[k] < budget[k]:
-                        t_tr[k] = min(th[k], budget[k])
-                        snap[k] = (b.positions(k), b.velocities(k), b.qpos(k))
-                t_prev = th.copy()
-                kstar, upto, done = settle(th)
-            # accept periods [0, upto) in full and, with a transition, the
-            # transition's period up to the transition
-            for k in range(upto):
-                self._period(k, budget[k], fr_sum[k], t_sum[k], False)
-            if kstar is not None:
-                self._period(kstar, t_tr[kstar], fr_sum[kstar], t_sum[kstar], True)
-                x, v, xq = snap[kstar]
-                self.time += budget[:kstar].sum() + t_tr[kstar]
-                self.log.transitions.append((self.m + kstar, float(self.slider_at(self.m + kstar)[0]), self.time))
-                self.t_in = (self.t_in if kstar == 0 else 0.0) + t_tr[kstar]
-                self.m += kstar
-                self.state.pos, self.state.vel, self.state.pos_ref = x, v, xq
-            else:
-                self.time += budget.sum()
-                self.state.pos, self.state.vel = b.positions(R - 1), b.velocities(R - 1)
-                self.state.pos_ref = b.ref(R - 1)
-                self.m += R
-                self.t_in = 0.0
-            self.state.slider = self.slider_at(self.m)
-            self.log.intervals += 1
-            return None if kstar is None else self.m
-        finally:
-            b.close()
-
-    def _prerun(self, b, R, accumulate):
-        """Unbiased MD at every position, then sigma_L, sigma_U per replica
-        from the slopes sampled during it (Eq. 14's band)."""
-        B = self.band
-        m = float(B["m"])
-        b.set_bias(np.tile([0.0, 0.0, 1.0, m], (R, 1)))
-        n = int(B["prerun"]) // int(B["sample_every"])
-        sig = np.empty((n, R))
-        for i in range(n):
-            b.step(int(B["sample_every"]))
-            ob = np.asarray(b.obs())
-            accumulate(ob)
-            sig[i] = ob[:, OBS_SIGMA]
-        self.log.md_steps += n * int(B["sample_every"])
-        lo, hi = np.quantile(sig, B["q_lo"], axis=0), np.quantile(sig, B["q_hi"], axis=0)
-        hi = np.maximum(hi, lo + 1e-12 * np.maximum(1.0, np.abs(lo)))
-        b.set_bias(np.column_stack([np.full(R, float(B["dvmax"])), lo, hi, np.full(R, m)]))
+    def _settings(self):
+        return (self.params, self.n_par, self.check_every, self.sample_every, self.theta, self.requench,
+                tuple(sorted(self.quench.items())), None if self.band is None else tuple(sorted(self.band.items())),
+                self.max_checks, self.make_batch)
 
     def _period(self, k, t, fr_sum, t_sum, transition):
         self.log.periods.append(Period(index=self.m + k, slider_x=float(self.slider_at(self.m + k)[0]), time=float(t),
@@ -253,6 +161,168 @@ class SteppedSliding:
         while self.m < target:
             self.interval()
         return self.log
+
+
+class _Interval:
+    """One driver's share of a batch during one interval: replicas
+    [off, off + n_par) of the batch."""
+
+    def __init__(self, d, off):
+        R = d.n_par
+        if d.t_in >= d.dtau:                # a transition closed the current position's period
+            d.m += 1
+            d.t_in = 0.0
+            d.state.slider = d.slider_at(d.m)
+        self.d, self.off, self.R = d, off, R
+        self.budget = np.full(R, d.dtau)
+        self.budget[0] = d.dtau - d.t_in
+        self.reps = d._replicas()
+        self.t_prev = np.zeros(R)           # boosted clocks at the last check
+        self.t_acc = np.zeros(R)            # boosted clocks at the last F_R sample
+        self.t_tr = np.full(R, np.inf)      # boosted time of a counted transition
+        self.fr_sum, self.t_sum = np.zeros(R), np.zeros(R)
+        self.snap = {}
+        self.end = None                     # (x, v, r_O) of the last replica when done
+        self.kstar, self.upto, self.done = None, R, False
+        self.checks = 0
+
+    def sl(self, a):
+        return a[self.off:self.off + self.R]
+
+    def flag(self, b, flags, th, at_start=False):
+        for k in range(self.R):
+            if flags[k] and not np.isfinite(self.t_tr[k]) and (at_start or self.t_prev[k] < self.budget[k]):
+                self.t_tr[k] = 0.0 if at_start else min(th[k], self.budget[k])
+                self.snap[k] = (b.positions(self.off + k), b.velocities(self.off + k), b.qpos(self.off + k))
+
+    def accumulate(self, ob):
+        # boost-weighted F_R over each open period, cut at its end
+        th = ob[:, OBS_T_H]
+        dt = np.clip(np.minimum(th, self.budget) - np.minimum(self.t_acc, self.budget), 0.0, None)
+        dt[np.isfinite(self.t_tr)] = 0.0
+        self.fr_sum += ob[:, OBS_FR] * dt
+        self.t_sum += dt
+        self.t_acc = th.copy()
+
+    def settle(self, b, th):
+        # the first position with a transition, the positions before it, and
+        # whether all of those have used up their periods
+        hit = np.nonzero(np.isfinite(self.t_tr))[0]
+        self.kstar = int(hit[0]) if hit.size else None
+        self.upto = self.kstar if self.kstar is not None else self.R
+        self.done = all(th[k] >= self.budget[k] for k in range(self.upto))
+        if self.done and self.kstar is None:
+            last = self.off + self.R - 1
+            self.end = (b.positions(last), b.velocities(last), b.ref(last))
+
+    def finish(self):
+        # accept periods [0, upto) in full and, with a transition, the
+        # transition's period up to the transition
+        d, kstar = self.d, self.kstar
+        for k in range(self.upto):
+            d._period(k, self.budget[k], self.fr_sum[k], self.t_sum[k], False)
+        if kstar is not None:
+            d._period(kstar, self.t_tr[kstar], self.fr_sum[kstar], self.t_sum[kstar], True)
+            x, v, xq = self.snap[kstar]
+            d.time += self.budget[:kstar].sum() + self.t_tr[kstar]
+            d.log.transitions.append((d.m + kstar, float(d.slider_at(d.m + kstar)[0]), d.time))
+            d.t_in = (d.t_in if kstar == 0 else 0.0) + self.t_tr[kstar]
+            d.m += kstar
+            d.state.pos, d.state.vel, d.state.pos_ref = x, v, xq
+        else:
+            d.time += self.budget.sum()
+            d.state.pos, d.state.vel, d.state.pos_ref = self.end
+            d.m += self.R
+            d.t_in = 0.0
+        d.state.slider = d.slider_at(d.m)
+        d.log.intervals += 1
+        return None if kstar is None else d.m
+
+
+def run_intervals(drivers):
+    """One interval of each SteppedSliding in `drivers`, all in one batch.
+
+    The drivers are independent runs (samples, each its own state and
+    replica ids) with the same settings.  Each keeps its own clocks, checks
+    and result; a driver whose interval has finished stops counting while
+    the others go on, and carries on from its state at that moment, so the
+    result of each equals that of its own interval() whenever a replica's
+    trajectory does not depend on the other replicas in the batch.  Returns
+    each driver's interval() value."""
+    if not drivers:
+        return []
+    d0 = drivers[0]
+    if any(d._settings() != d0._settings() for d in drivers[1:]):
+        raise ValueError("run_intervals: the drivers must share params, n_par, check/sample intervals, "
+                         "theta, quench, requench, band, max_checks and make_batch")
+    ivs, off = [], 0
+    for d in drivers:
+        ivs.append(_Interval(d, off))
+        off += d.n_par
+    b = d0.make_batch([r for iv in ivs for r in iv.reps], d0.params)
+    try:
+        zeros = np.zeros(off)
+        if d0.requench:
+            flags = np.asarray(b.quench(theta=d0.theta, adopt=2, **d0.quench))
+            for iv in ivs:
+                iv.flag(b, iv.sl(flags), None, at_start=True)
+        for iv in ivs:
+            iv.settle(b, iv.sl(zeros))
+        if d0.band is not None and not all(iv.done for iv in ivs):
+            _prerun(b, d0.band, [iv for iv in ivs if not iv.done], off)
+        while not all(iv.done for iv in ivs):
+            open_ = [iv for iv in ivs if not iv.done]
+            for iv in open_:
+                if iv.checks == d0.max_checks:
+                    raise RuntimeError("interval did not finish within max_checks quench checks")
+                iv.checks += 1
+            for _ in range(d0.check_every // d0.sample_every):
+                b.step(d0.sample_every)
+                ob = np.asarray(b.obs())
+                for iv in open_:
+                    iv.d.log.md_steps += d0.sample_every
+                    iv.accumulate(iv.sl(ob))
+            th_all = ob[:, OBS_T_H]
+            flags = np.asarray(b.quench(theta=d0.theta, adopt=0, **d0.quench))
+            for iv in open_:
+                th = iv.sl(th_all)
+                iv.flag(b, iv.sl(flags), th)
+                iv.t_prev = th.copy()
+                iv.settle(b, th)
+        return [iv.finish() for iv in ivs]
+    finally:
+        b.close()
+
+
+def _prerun(b, band, open_, nrep):
+    """Unbiased MD at every position, then sigma_L, sigma_U per replica
+    from the slopes sampled during it (Eq. 14's band)."""
+    m = float(band["m"])
+    b.set_bias(np.tile([0.0, 0.0, 1.0, m], (nrep, 1)))
+    n = int(band["prerun"]) // int(band["sample_every"])
+    sig = np.empty((n, nrep))
+    for i in range(n):
+        b.step(int(band["sample_every"]))
+        ob = np.asarray(b.obs())
+        for iv in open_:
+            iv.accumulate(iv.sl(ob))
+        sig[i] = ob[:, OBS_SIGMA]
+    for iv in open_:
+        iv.d.log.md_steps += n * int(band["sample_every"])
+    lo, hi = np.quantile(sig, band["q_lo"], axis=0), np.quantile(sig, band["q_hi"], axis=0)
+    hi = np.maximum(hi, lo + 1e-12 * np.maximum(1.0, np.abs(lo)))
+    b.set_bias(np.column_stack([np.full(nrep, float(band["dvmax"])), lo, hi, np.full(nrep, m)]))
+
+
+def run_ensemble(drivers, n_positions):
+    """Advance every driver until its slider has taken n_positions more
+    steps, running the unfinished ones together interval by interval."""
+    target = {id(d): d.m + int(n_positions) for d in drivers}
+    while True:
+        open_ = [d for d in drivers if d.m < target[id(d)]]
+        if not open_:
+            return [d.log for d in drivers]
+        run_intervals(open_)
 
 
 class ContinuousSliding:

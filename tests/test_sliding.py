@@ -311,3 +311,49 @@ def test_oracle_backed_sliding_through_a_slip(oracle_mod):
     # loading before the slip: F_R grows with the slider position
     frs = [p.fr_mean for p in d.log.periods if not p.transition]
     assert len(frs) >= 2 and frs[-1] > frs[0]
+
+
+def test_ensemble_in_one_batch_equals_separate_runs(oracle_mod):
+    """Three samples (own states and replica ids, one seed) run together in
+    one oracle-backed batch per interval give exactly the logs and states of
+    three separate runs: a sample whose interval ends early (a slip) stops
+    counting and carries on from its state at that moment."""
+    from paper_0909_5215_gb300 import model as M
+    from paper_0909_5215_gb300.sliding import SteppedSliding, run_ensemble, run_intervals
+    base = small2d(kT=0.02)
+    p = M.Params(prec=0, bias_on=0, seed=5)
+    xq, _, _ = oracle_mod.OracleReplica(base, p).quench(method=1, ftol=1e-6, max_iter=20000)
+    mk = lambda reps, params: OracleBatch(reps, params, oracle_mod)
+
+    def drivers():
+        out = []
+        for s in range(3):
+            st = base.copy()
+            st.pos, st.pos_ref, st.rep_id = xq.copy(), xq.copy(), 50 + s
+            o = oracle_mod.OracleReplica(st, p)
+            o.run(200 + 100 * s)
+            st.pos, st.vel = o.x.copy(), o.v.copy()
+            out.append(SteppedSliding(st, p, dx=0.2, v_s=0.4, n_par=4, check_every=100, sample_every=20,
+                                      quench=dict(method=1, ftol=1e-4, max_iter=3000), make_batch=mk,
+                                      rep_id0=1000 * (s + 1)))
+        return out
+
+    together, apart = drivers(), drivers()
+    run_ensemble(together, 16)
+    for d in apart:
+        while d.m < 16:
+            d.interval()
+    assert sum(len(d.log.transitions) for d in apart) >= 1
+    for a, t in zip(apart, together):
+        assert t.m == a.m and t.time == a.time and t.t_in == a.t_in
+        assert t.log.md_steps == a.log.md_steps and t.log.intervals == a.log.intervals
+        assert t.log.transitions == a.log.transitions
+        assert [(q.index, q.time, q.transition) for q in t.log.periods] == \
+               [(q.index, q.time, q.transition) for q in a.log.periods]
+        assert np.array_equal([q.fr_mean for q in t.log.periods], [q.fr_mean for q in a.log.periods], equal_nan=True)
+        assert np.array_equal(t.state.pos, a.state.pos) and np.array_equal(t.state.pos_ref, a.state.pos_ref)
+    # drivers with different settings cannot share a batch
+    d1, d2 = drivers()[:2]
+    d2.check_every = 200
+    with pytest.raises(ValueError):
+        run_intervals([d1, d2])
