@@ -197,7 +197,7 @@ def oracle_sample(name, seconds, threads_hint=None):
     return {"value": atoms * m / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
             "sample": "%d of %d replicas x %d BAOAB steps (list, LJ+H.dr, bias, Langevin; quench excluded), "
                       "%.1f s" % (S, len(reps), m, dt),
-            "hypertime_per_s": th / dt, "seconds": dt}
+            "hypertime_per_s": th / dt, "hypertime_per_s_per_replica": th / dt / S, "seconds": dt}
 
 
 def run_reference(args):
@@ -207,17 +207,19 @@ def run_reference(args):
     per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(args.workload, per / 4)
-    vals, ths, secs, last = [], [], 0.0, None
+    vals, ths, thr, secs, last = [], [], [], 0.0, None
     for _ in range(args.steps):
         last = oracle_sample(args.workload, per)
         vals.append(last["value"])
         ths.append(last["hypertime_per_s"])
+        thr.append(last["hypertime_per_s_per_replica"])
         secs += last["seconds"]
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "hypertime_per_s": float(np.mean(ths)),
+            "hypertime_per_s_per_replica": float(np.mean(thr)),
             "config": {"workload": args.workload, "sample": last["sample"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
@@ -417,7 +419,7 @@ def run_ours(args):
                        "precision": "split: FP32 pair/bias arithmetic, FP64 positions, sums, clocks" if split
                        else "FP64 throughout", "l2": "inputs larger than L2 (%.0f MB workspace)" % (
                            b.ws_bytes / 1e6), "parallelism": "replicas" if world == 1 else "replicas x%d ranks" % world},
-            "hypertime_per_s": dth / sec,
+            "hypertime_per_s": dth / sec, "hypertime_per_s_per_replica": dth / sec / len(reps),
             "md_only": {"value": atom_steps / (md_ms / 1000.0), "unit": UNIT},
             "roofline": roof, "phases_ms": phases, "fp64_form": fp64,
             "list_rebuilds_per_replica_step": float((ob1[:, 12] - ob0[:, 12]).sum()) / (len(reps) * args.md_steps *
