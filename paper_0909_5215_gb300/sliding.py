@@ -40,7 +40,7 @@ position that sets r_O (requench).  A replica whose quench already lands more
 than theta from the carried r_O has lost its basin at that position: it makes
 its transition at the start of its period.  With `band`, each replica also
 runs an unbiased pre-run at its position and takes sigma_L and sigma_U as
-quantiles of the slopes sampled there (the pre-simulation of Sec. 3.1.2); the
+quantiles of the slopes sampled there (the pre-simulation of Sec. 3.1.3); the
 pre-run is ordinary MD and counts toward the period.
 
 ContinuousSliding runs the reference method the stepped scheme replaces: the
