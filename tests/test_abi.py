@@ -101,6 +101,34 @@ def test_workspace_sizing_host_only(hdlib):
     assert hdlib.workspace_bytes([small2d()], p, maxnb=1000) == 0
 
 
+def test_empty_and_degenerate_batches_size_to_zero(hdlib):
+    """The host checks that run before any device work: no replicas, a
+    replica without atoms, non-finite or out-of-plane positions, bad roles,
+    types or temperatures all give 0 bytes (hd_create: HD_ERR_ARG)."""
+    from paper_0909_5215_gb300 import model as M
+    p = M.Params(prec=1)
+    descs, keep = hdlib.make_descs([small2d()])
+    assert hdlib.hd_workspace_bytes(descs, 0, hdlib.make_params(p)) == 0
+    del keep
+
+    def sized(mutate):
+        r = small2d()
+        r.pos, r.role, r.type = r.pos.copy(), r.role.copy(), r.type.copy()
+        mutate(r)
+        return hdlib.workspace_bytes([r], p)
+
+    assert sized(lambda r: None) > 0
+    def empty(r):
+        r.pos, r.role, r.type = r.pos[:0], r.role[:0], r.type[:0]
+    assert sized(empty) == 0
+    assert sized(lambda r: r.pos.__setitem__((3, 0), np.nan)) == 0
+    assert sized(lambda r: r.pos.__setitem__((3, 1), np.inf)) == 0
+    assert sized(lambda r: r.pos.__setitem__((3, 2), 0.5)) == 0         # 2-D needs z == 0
+    assert sized(lambda r: r.type.__setitem__(0, 2)) == 0
+    assert sized(lambda r: setattr(r, "kT", 0.0)) == 0
+    assert sized(lambda r: setattr(r, "m_exp", 0)) == 0
+
+
 def test_create_rejects_bad_arguments_before_any_device_work(hdlib):
     import ctypes as C
     from paper_0909_5215_gb300 import model as M
