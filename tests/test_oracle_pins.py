@@ -373,3 +373,21 @@ def test_transition_flag(oracle_mod):
     xq2, _, _ = o2.quench(method=1, ftol=1e-6, max_iter=40000)
     flag2, md2 = o2.transition(xq2, 0.5)
     assert flag2 and md2 > 0.9
+
+
+def test_diverging_quench_stops_cleanly(oracle_mod):
+    """Steepest descent with a step beyond 2 / (largest curvature) runs away
+    from a thermal configuration of the paper's 2-D model: the quench must
+    stop early with fmax = NaN, not build a cell grid from runaway
+    coordinates, and leave the MD state alone."""
+    from paper_0909_5215_gb300 import model as M
+    base = M.paper2d(kT=0.01)
+    st = thermalise(base, amp=0.05, seed=4)
+    o = oracle_mod.OracleReplica(st, _params())
+    x0 = o.x.copy()
+    xq, it, fm = o.quench(method=0, ftol=1e-4, max_iter=2000, step_size=0.05)
+    assert np.isnan(fm) and it < 2000
+    assert np.array_equal(o.x, x0)
+    # the same state with a stable step converges
+    xq, it, fm = o.quench(method=0, ftol=1e-4, max_iter=200000, step_size=0.002)
+    assert fm < 1e-4
