@@ -21,3 +21,31 @@ def test_choose_and_cache(tmp_path):
     assert (drv2, blk2) == (drv, blk) and len(calls) == len(autotune.CANDIDATES)
     assert autotune.signature(reps, p) != autotune.signature(reps[:1], p)
     assert autotune.choose({(1, 64): None, (1, 128): None}) == (hd.HD_DRIVER_KERNELS, 128)
+
+
+def test_rebuilt_library_or_corrupt_cache_is_tuned_afresh(tmp_path, monkeypatch):
+    from paper_0909_5215_gb300 import autotune, hd
+    from paper_0909_5215_gb300 import model as M
+    reps = [small2d()]
+    p = M.Params(prec=1)
+    calls = []
+
+    def fake(rs, params, driver, block, steps, warm):
+        calls.append((driver, block))
+        return 1.0 if (driver, block) == (hd.HD_DRIVER_KERNELS, 64) else 2.0
+
+    cache = str(tmp_path / "sub" / "tune.json")
+    monkeypatch.setattr(autotune, "build_identity", lambda: "lib1:1|GPU A")
+    assert autotune.tune(reps, p, cache=cache, timer=fake)[:2] == (hd.HD_DRIVER_KERNELS, 64)
+    n = len(calls)
+    autotune.tune(reps, p, cache=cache, timer=fake)
+    assert len(calls) == n                                  # same build: cached
+    monkeypatch.setattr(autotune, "build_identity", lambda: "lib2:2|GPU A")
+    autotune.tune(reps, p, cache=cache, timer=fake)
+    assert len(calls) == 2 * n                              # rebuilt library: timed again
+    with open(cache, "w") as f:
+        f.write("{not json")
+    autotune.tune(reps, p, cache=cache, timer=fake)
+    assert len(calls) == 3 * n                              # unreadable cache: timed again
+    # every candidate failing falls back to the per-phase kernels
+    assert autotune.choose({c: None for c in autotune.CANDIDATES}) == (hd.HD_DRIVER_KERNELS, 128)
