@@ -332,7 +332,7 @@ def workload_states(oracle_mod):
 
 
 def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_states):
-    """Spec tolerance: DeltaV and t_h within 1e-6 (relative) of the FP64
+    """The split form's bound: DeltaV and t_h within 1e-6 (relative) of the FP64
     oracle after 100 steps from one state, split form."""
     b, ors = batch_and_oracles(hd, oracle_mod, workload_states, 1)
     for k, o in enumerate(ors):
