@@ -123,8 +123,10 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p,
 
 /* Move the sliders: slider[2*r], slider[2*r+1] = (x_S, y_S) of replica r
  * (stepped sliding, Sec. 2.3 and Fig. 1).  If requench_ref is non-zero, each
- * replica is then quenched (FIRE, ftol 1e-6, at most 20000 steps) and r_O
- * is set to the result. */
+ * replica is then quenched (FIRE from dt0 = 0.005, at most 20000 steps, to
+ * ftol 1e-6 in the FP64 form and 1e-4 in the split form, whose FP32 pair
+ * forces do not resolve the rigid body's summed force below that) and r_O
+ * is set to the result where the quench converged (HD_OBS_QCONV). */
 hd_status hd_set_slider(hd_ctx *ctx, const double *slider, int requench_ref);
 
 /* Replace the bias parameters of Eq. 14: bias[4*r .. 4*r+3] =
@@ -141,9 +143,10 @@ hd_status hd_step(hd_ctx *ctx, int n_steps);
  * made.  A replica whose quenched positions lie more than theta from r_O
  * (any atom, minimum image) is flagged as having made a transition
  * (Sec. 2.3).  adopt: 0 keep r_O; 1 set r_O to the quenched positions of
- * flagged replicas; 2 of every replica.  h_flags [n_rep] (may be NULL)
- * receives the flags; the call synchronises the stream.  The MD state is
- * not changed. */
+ * flagged replicas; 2 of every replica.  Only a replica whose quench reached
+ * ftol adopts: an unconverged quench is no basin minimum (HD_OBS_QCONV says
+ * which converged).  h_flags [n_rep] (may be NULL) receives the flags; the
+ * call synchronises the stream.  The MD state is not changed. */
 hd_status hd_quench(hd_ctx *ctx, int method, double ftol, int max_iter, double step_size,
                     double theta, int adopt, int32_t *h_flags);
 
@@ -169,7 +172,12 @@ enum {
     HD_OBS_DV = 5, HD_OBS_SIGMA = 6, HD_OBS_D = 7, HD_OBS_FR = 8, HD_OBS_XT = 9,
     HD_OBS_YT = 10, HD_OBS_ZT = 11, HD_OBS_NREBUILD = 12, HD_OBS_BOOST = 13,
     HD_OBS_QITER = 14, HD_OBS_QFMAX = 15, HD_OBS_G = 16, HD_OBS_FBODY = 17,
-    HD_OBS_VBODY = 20, HD_OBS_QDISP = 23, HD_OBS_LEN = 24
+    HD_OBS_VBODY = 20, HD_OBS_QDISP = 23,
+    HD_OBS_NDV_ZERO = 24,      /* steps taken so far with DeltaV = 0 (sigma <= sigma_L) */
+    HD_OBS_NDV_BAND = 25,      /* ... with 0 < DeltaV < DeltaV_max                    */
+    HD_OBS_NDV_MAX = 26,       /* ... with DeltaV = DeltaV_max (sigma >= sigma_U)      */
+    HD_OBS_QCONV = 27,         /* 1 if the last quench reached ftol, else 0            */
+    HD_OBS_LEN = 28
 };
 
 hd_status hd_read(hd_ctx *ctx, int field, int replica, void *h_dst, size_t bytes);
@@ -205,11 +213,17 @@ hd_status hd_timing(hd_ctx *ctx, int enable, double out[8]);
  * most 64 atoms and maxnb <= 160; larger inputs return HD_ERR_ARG.  Each GPU
  * that loads the library holds that array (about 5.4 MB) until the process
  * exits.  The first call on a device looks up the array's address with that
- * device current; make that first call before any stream capture.  Every
- * call shares the array and leaves its contents behind; counts and the
- * error word are cleared at the start of each call, and calls that overlap
- * on the GPU race.  Synchronises cuda_stream; returns HD_ERR_OVERFLOW if a
- * row or a cell exceeded its capacity. */
+ * device current; under CUDA's lazy module loading that call also commits
+ * the module and the array on the device, so it can fail (HD_ERR_CUDA) in a
+ * program that has already reserved all of the GPU's memory: make the first
+ * call at start-up, before reserving memory, or run with
+ * CUDA_MODULE_LOADING=EAGER.  Every call synchronises cuda_stream (it reads
+ * back an error word and, with an open axis, the positions' extent), so it
+ * cannot be called while that stream is being captured.  Every call shares
+ * the array and leaves its contents behind; counts, extent and the error
+ * word are cleared at the start of each call, and calls that overlap on the
+ * GPU race.  Returns HD_ERR_OVERFLOW if a row or a cell exceeded its
+ * capacity, HD_ERR_NUMERIC for a non-finite position on an open axis. */
 hd_status hd_nlist_static(const double *d_pos, int n_atoms, const double box[3], const uint8_t periodic[3],
                           double rl, int maxnb, int32_t *d_nbr, int32_t *d_nnb, void *cuda_stream);
 

@@ -104,15 +104,31 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
         int nrig = 0;
         for (int i = 0; i < d.n_atoms; ++i) nrig += d.role[i] == 2;
         R.nrig = nrig;
-        // geometry, fixed point and cells
+        // geometry, fixed point and cells.  The pair sweep's fixed point counts
+        // 2^(32+k) units per periodic length L, k = max(0, floor(log2(L / (8 rl)))):
+        // the int32 difference of two images is then the exact minimum image of
+        // every pair closer than L / 2^(k+1) >= 4 rl, which covers every pair the
+        // list build tests (at most two cell widths apart) while the unit stays
+        // at L / 2^(32+k) <= 16 rl / 2^32 whatever the box length.
+        auto kfine = [&](double len) {
+            int k = 0;
+            while (k < 16 && len / std::ldexp(1.0, k + 1) >= 8.0 * rl) ++k;
+            return k;
+        };
+        bool same = true;
+        for (int q = 0; q < d.dim - 1; ++q) same &= d.box[q] == d.box[0];
         for (int a = 0; a < 3; ++a) {
             R.periodic[a] = (a < d.dim && d.periodic[a]) ? 1 : 0;
             if (R.periodic[a]) {
+                const int k = kfine(d.box[a]);
+                const double units = std::ldexp(4294967296.0, k);
                 R.L[a] = d.box[a];
                 R.invL[a] = 1.0 / d.box[a];
-                R.fx_scale[a] = 4294967296.0 / d.box[a];
+                R.fx_scale[a] = units / d.box[a];
                 R.fx_origin[a] = 0.0;
-                R.fx_lsb[a] = (float)(d.box[a] / 4294967296.0);
+                R.fx_lsb[a] = (float)(d.box[a] / units);
+                R.bin_scale[a] = 4294967296.0 / d.box[a];
+                if (a == 0) R.fine_shift = k;
                 int nc = (int)std::floor(d.box[a] / (rl * (1.0 + 1e-6)));
                 R.nc[a] = nc >= 3 ? nc : 1;
             } else if (a < d.dim) {
@@ -122,21 +138,22 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                     mx = std::max(mx, d.pos[3 * i + a]);
                 }
                 // Common fixed-point unit: when every periodic axis has the same
-                // length L, the open axis uses L 2^k / 2^32 per unit, so squared
-                // distances are exact integer sums in units of (L / 2^32)^2.
+                // length L, the open axis uses span = L 2^z (z >= 0) per 2^(32+k)
+                // units, so squared distances are exact integer sums in units of
+                // (L / 2^(32+k))^2.
                 const double need = 2.0 * (mx - mn) + 24.0;
-                bool same = true;
-                for (int q = 0; q < d.dim - 1; ++q) same &= d.box[q] == d.box[0];
                 double span;
+                int k;
                 if (same && d.box[0] > 2.0 * (p->rc + 0.5)) {
-                    int k = 0;
+                    int z = 0;
                     span = d.box[0];
-                    while (span < need) { span *= 2.0; ++k; }
+                    while (span < need) { span *= 2.0; ++z; }
+                    k = kfine(d.box[0]);
                     R.exact_r2 = 1;
-                    R.zshift = k;
-                    R.shift_y = a == 1 ? k : 0;
-                    R.shift_z = a == 2 ? k : 0;
-                    const double u = d.box[0] / 4294967296.0, u2 = u * u;
+                    R.zshift = z;
+                    R.shift_y = a == 1 ? z : 0;
+                    R.shift_z = a == 2 ? z : 0;
+                    const double u = d.box[0] / std::ldexp(4294967296.0, k), u2 = u * u;
                     R.u2_42 = (float)(u2 * 4398046511104.0);
                     R.u2lo_42 = (float)(u2 * 4398046511104.0 - (double)R.u2_42);
                     R.u2_21 = (float)(u2 * 2097152.0);
@@ -144,15 +161,17 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                 } else {
                     span = 64.0;
                     while (span < need) span *= 2.0;
+                    k = kfine(span);
                 }
+                const double units = std::ldexp(4294967296.0, k);
                 R.fx_origin[a] = 0.5 * (mn + mx);
-                R.fx_scale[a] = 4294967296.0 / span;
-                R.fx_lsb[a] = (float)(span / 4294967296.0);
+                R.fx_scale[a] = units / span;
+                R.fx_lsb[a] = (float)(span / units);
                 R.open_lim = 0.5 * span - 4.0;
                 const double w = rl * (1.0 + 1e-4), lo = mn - 2.0;
                 R.nc[a] = std::max(1, (int)std::ceil((mx + 2.0 - lo) / w));
-                R.cell_lo_fix = (long long)std::llrint((lo - R.fx_origin[a]) * R.fx_scale[a]);
-                R.cell_inv_w_lsb = (float)((span / 4294967296.0) / w);
+                R.cell_lo = lo;
+                R.cell_inv_w = 1.0 / w;
             } else {
                 R.nc[a] = 1;
             }
@@ -174,7 +193,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                     double x = d.pos[3 * i + a];
                     double t;
                     if (R.periodic[a]) t = (x - R.L[a] * std::floor(x / R.L[a])) / R.L[a] * R.nc[a];
-                    else t = (x - (R.fx_origin[a] + R.cell_lo_fix / R.fx_scale[a])) / (rl * (1.0 + 1e-4));
+                    else t = (x - R.cell_lo) * R.cell_inv_w;
                     c[a] = std::min(R.nc[a] - 1, std::max(0, (int)std::floor(t)));
                 }
                 key[i] = (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
@@ -293,7 +312,7 @@ struct hd_ctx {
     std::map<std::string, cudaGraphExec_t> qgraphs;
     bool persist_graph_ok = true;
     std::vector<double> qdisp;
-    std::vector<int> qflag;
+    std::vector<int> qflag, qconv;
     long long h2d = 0, d2h = 0;
     // timing: events recorded around phases; harvested at hd_timing / next step
     int timing = 0;
@@ -692,6 +711,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     CK(cudaGetLastError());
     c->qdisp.assign(P.nrep, 0.0);
     c->qflag.assign(P.nrep, 0);
+    c->qconv.assign(P.nrep, 0);
     if (p->driver == HD_DRIVER_PERSISTENT && setup_persistent(c)) c->driver = HD_DRIVER_PERSISTENT;
     return check_device(c);
 }
@@ -711,7 +731,9 @@ hd_status hd_set_slider(hd_ctx *c, const double *slider, int requench_ref) {
     launch_scalar(c->D, 0, c->s);
     c->launches += 1;
     CK(cudaGetLastError());
-    if (requench_ref) return hd_quench(c, 1, 1e-6, 20000, 0.01, 1e300, 2, nullptr);
+    // FIRE from dt0 = 0.005 (fastest on thermal LJ states); the split form's
+    // FP32 pair forces reach 1e-4 but not 1e-6 on the rigid body's sum
+    if (requench_ref) return hd_quench(c, 1, c->P.prec == HD_FP64 ? 1e-6 : 1e-4, 20000, 0.005, 1e300, 2, nullptr);
     return HD_OK;
 }
 
@@ -882,8 +904,12 @@ hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double ste
         memcpy(&m, &qd[r], 8);
         c->qdisp[r] = std::sqrt(m);
         c->qflag[r] = std::sqrt(m) > theta;
+        // st[] holds the state after the last chunk: q_fmax is that of the
+        // final positions (the iteration that found fmax < ftol moved nothing)
+        c->qconv[r] = st[r].q_fmax < ftol;
         if (h_flags) h_flags[r] = c->qflag[r];
-        ad[r] = adopt == 2 || (adopt == 1 && c->qflag[r]);
+        // an unconverged quench is no basin minimum: it never becomes r_O
+        ad[r] = c->qconv[r] && (adopt == 2 || (adopt == 1 && c->qflag[r]));
         any |= ad[r] != 0;
     }
     if (any) {
@@ -1025,6 +1051,8 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
             o[HD_OBS_VBODY + a] = S.vbody_full[a];
         }
         o[HD_OBS_QDISP] = c->qdisp.empty() ? 0.0 : c->qdisp[replica];
+        for (int a = 0; a < 3; ++a) o[HD_OBS_NDV_ZERO + a] = (double)S.n_dv[a];
+        o[HD_OBS_QCONV] = c->qconv.empty() ? 0.0 : (double)c->qconv[replica];
         return HD_OK;
     }
     default:

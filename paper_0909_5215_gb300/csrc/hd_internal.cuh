@@ -18,10 +18,14 @@
 //   per tile (block atoms of one replica): NPART FP64 partial sums, FP64 K part
 //   per replica: RepDev (settings), RepState (clocks, body), Scal (scalars)
 //
-// Fixed point: on a periodic axis x_fix = rint(x * 2^32 / L) taken modulo 2^32,
-// so the int32 difference of two atoms is the minimum image exactly; on the
-// open axis x_fix = rint((x - origin) * 2^32 / span) with |x - origin| kept
-// below span / 2 - 4 (checked every step).
+// Fixed point: on a periodic axis x_fix = rint(x * 2^(32+k) / L) taken modulo
+// 2^32 (k = fine_shift >= 0), so the int32 difference of two images is the
+// exact minimum image of every pair closer than L / 2^(k+1); k is chosen so
+// that this covers every pair the list build tests (at most two cell widths
+// apart).  On the open axis x_fix = rint((x - origin) * 2^(32+k) / span) with
+// span >= L.  Cells are computed from the FP64 positions (exact integer map
+// x * 2^32 / L on periodic axes, FP64 quotient on the open axis), and
+// |x - origin| stays below span / 2 - 4 (checked every step).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -65,10 +69,12 @@ struct RepDev {
     double dvmax, sig_lo, sig_hi;
     double eps[2][2], sig2[2][2], shift[2][2];
     float epsf[2][2], sig2f[2][2], shiftf[2][2];
+    // fine fixed point of the pair sweep: q = rint((x - origin) * scale) mod 2^32
     double fx_scale[3], fx_origin[3];
     float fx_lsb[3];
-    float cell_inv_w_lsb;        // open axis: cells per fixed-point unit
-    long long cell_lo_fix;       // open axis: fixed-point origin of the cell grid
+    int fine_shift;              // periodic axes count 2^(32 + fine_shift) units per L
+    double bin_scale[3];         // periodic axes: 2^32 / L, the exact integer cell map
+    double cell_lo, cell_inv_w;  // open axis: origin and inverse width of the cell grid
     double open_lim;             // escape bound |x - origin| on the open axis
     double kr_n;                 // k / n_rig (spring Hessian per rigid atom)
     float kr_nf, c_ouf, s_ouf, pad1;
@@ -84,6 +90,7 @@ struct RepDev {
 struct RepState {
     double t_h, t_md, vbody[3], vbody_full[3], K;
     long long step, n_rebuild;
+    long long n_dv[3];           // steps with DeltaV = 0, inside the band, at DeltaV_max
     // quench
     double q_dt, q_alpha, q_vb[3], q_fmax, q_disp;
     int q_npos, q_iter, q_done, q_flag;
@@ -207,14 +214,17 @@ __device__ __forceinline__ int4 fix_pos(const RepDev &R, dbl4 x, int w) {
     return make_int4(fix_coord(R, 0, x.x), fix_coord(R, 1, x.y), fix_coord(R, 2, x.z), w);
 }
 
-// Cell of a fixed-point position: exact integer map on periodic axes,
-// clamped linear map on the open axis.
-__device__ __forceinline__ int cell_axis(const RepDev &R, int a, int q) {
-    int nc = R.nc[a];
+// Cell of an FP64 coordinate: exact integer map on periodic axes (the image
+// rint(x 2^32 / L) mod 2^32 times nc, top 32 bits), clamped FP64 quotient on
+// the open axis.
+__device__ __forceinline__ int cell_of(const RepDev &R, int a, double x) {
+    const int nc = R.nc[a];
     if (nc <= 1) return 0;
-    if (R.periodic[a]) return (int)(((unsigned long long)(unsigned int)q * (unsigned long long)nc) >> 32);
-    float t = (float)((long long)q - R.cell_lo_fix) * R.cell_inv_w_lsb;
-    int c = (int)floorf(t);
+    if (R.periodic[a]) {
+        const unsigned q = (unsigned)(unsigned long long)__double2ll_rn(x * R.bin_scale[a]);
+        return (int)(((unsigned long long)q * (unsigned long long)nc) >> 32);
+    }
+    const int c = (int)floor((x - R.cell_lo) * R.cell_inv_w);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 

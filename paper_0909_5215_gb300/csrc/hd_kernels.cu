@@ -153,7 +153,8 @@ __device__ __forceinline__ void dev_bin(const Dev &D, int t) {
     const int i = D.tile_start[t] + threadIdx.x;
     const RepDev &R = D.rep[r];
     const int4 p = D.rec[i].p;
-    const int cx = cell_axis(R, 0, p.x), cy = cell_axis(R, 1, p.y), cz = cell_axis(R, 2, p.z);
+    const dbl4 x = D.x[i];
+    const int cx = cell_of(R, 0, x.x), cy = cell_of(R, 1, x.y), cz = cell_of(R, 2, x.z);
     D.cellid[i] = cx | (cy << 10) | (cz << 20);
     const int c = R.cell0 + (cz * R.nc[1] + cy) * R.nc[0] + cx;
     const int slot = atomicAdd(&D.cell_cnt[c], 1);
@@ -620,6 +621,7 @@ __device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, do
         S.t_h += h * exp(dV / R.kT);
         S.t_md += h;
         S.step += 1;
+        S.n_dv[dV <= 0.0 ? 0 : (dV >= R.dvmax ? 2 : 1)] += 1;
         if (nr > 0)
             for (int a = 0; a < dim; ++a) vb[a] += 0.5 * h * fb[a] / (double)nr;
     }

@@ -10,10 +10,17 @@
 // library holds until the process exits.
 //
 // The first call on a device looks up that array's device address
-// (cudaGetSymbolAddress, with that device current) and keeps it; make that
-// first call before any stream capture.  Every call shares the array and it
-// keeps the last call's contents: the counts and the error word are cleared
-// at the start of each call, and calls that overlap on the GPU race.
+// (cudaGetSymbolAddress, with that device current) and keeps it.  Under
+// CUDA's lazy module loading that first call is also when the module, and
+// with it the array, is committed on the device, so it can itself fail for
+// want of memory: make it at start-up, before the program reserves the rest
+// of the GPU's memory (or run with CUDA_MODULE_LOADING=EAGER).  Every call
+// synchronises its stream (it reads back the error word and, with an open
+// axis, the extent of the positions), so no call may be made while that
+// stream is being captured into a graph.  Every call shares the array and
+// it keeps the last call's contents: the counts, the extent and the error
+// word are cleared at the start of each call, and calls that overlap on the
+// GPU race.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -32,6 +39,7 @@ struct StaticScratch {
     int cellid[S_MAX_ATOMS];
     int cell_cnt[S_MAX_CELLS];
     int cell_atoms[S_MAX_CELLS * S_CELL_CAP];
+    unsigned long long ext[6];   // per axis: min then max of the positions, order-preserving bits
     int err[4];
 };
 
@@ -39,18 +47,45 @@ static __device__ __align__(256) StaticScratch g_static_scratch;
 
 struct Grid {
     int nc[3], periodic[3];
-    double L[3], invL[3], scale[3], origin[3], lo[3], w[3];
+    double L[3], invL[3], scale[3], origin[3], lo[3], inv_w[3];
     float lsb[3];
     double rl2;
     float rl2_lo, rl2_hi;
 };
 
-__device__ __forceinline__ int s_cell(const Grid &G, int a, int q) {
+// Cell along one axis: exact integer map of the fixed-point image on a
+// periodic axis; FP64 quotient on an open axis (an FP32 quotient would round
+// by more than the cells' 1e-4 width margin near 1000 cells).
+__device__ __forceinline__ int s_cell(const Grid &G, int a, int q, double x) {
     if (G.nc[a] <= 1) return 0;
     if (G.periodic[a]) return (int)(((unsigned long long)(unsigned int)q * (unsigned long long)G.nc[a]) >> 32);
-    const float t = (float)((double)q / G.scale[a] + G.origin[a] - G.lo[a]) / (float)G.w[a];
-    const int c = (int)floorf(t);
+    const int c = (int)floor((x - G.lo[a]) * G.inv_w[a]);
     return c < 0 ? 0 : (c >= G.nc[a] ? G.nc[a] - 1 : c);
+}
+
+// Order-preserving map of a double onto unsigned 64-bit integers, so that
+// integer atomicMin/atomicMax give the FP64 minimum and maximum.
+__device__ __forceinline__ unsigned long long ord_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double ord_value(unsigned long long u) {
+    const unsigned long long b = (u >> 63) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+}
+
+// Extent of the positions along every axis (ext must hold +inf / -inf bits:
+// all ones for the minima, zero for the maxima).
+__global__ void k_s_extent(StaticScratch *S, const double *pos, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < 3; ++a) {
+        const unsigned long long u = ord_bits(pos[3 * i + a]);
+        atomicMin(&S->ext[2 * a], u);
+        atomicMax(&S->ext[2 * a + 1], u);
+    }
 }
 
 __device__ __forceinline__ double s_r2(const Grid &G, const double *a, const double *b) {
@@ -72,7 +107,8 @@ __global__ void k_s_bin(StaticScratch *S, Grid G, const double *pos, int n) {
         q[a] = (int)(unsigned int)(unsigned long long)v;
     }
     S->pfix[i] = make_int4(q[0], q[1], q[2], 0);
-    const int cx = s_cell(G, 0, q[0]), cy = s_cell(G, 1, q[1]), cz = s_cell(G, 2, q[2]);
+    const int cx = s_cell(G, 0, q[0], pos[3 * i]), cy = s_cell(G, 1, q[1], pos[3 * i + 1]),
+              cz = s_cell(G, 2, q[2], pos[3 * i + 2]);
     S->cellid[i] = cx | (cy << 10) | (cz << 20);
     const int c = (cz * G.nc[1] + cy) * G.nc[0] + cx;
     const int slot = atomicAdd(&S->cell_cnt[c], 1);
@@ -172,25 +208,26 @@ extern "C" hd_status hd_nlist_static(const double *d_pos, int n_atoms, const dou
     G.rl2 = rl * rl;
     G.rl2_lo = (float)(G.rl2 * (1.0 - 1.0 / 4096.0));
     G.rl2_hi = (float)(G.rl2 * (1.0 + 1.0 / 4096.0));
-    // the open-axis extent needs the positions' range, read back through a
-    // fixed host buffer on the stack
+    // the open-axis extent: one reduction kernel into the scratch array, one
+    // 48-byte read-back
     double mn[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
     bool need_ext = false;
     for (int a = 0; a < 3; ++a) need_ext |= !periodic[a];
     if (need_ext) {
-        double buf[3 * 512];
-        for (int a = 0; a < 3; ++a) { mn[a] = 1e300; mx[a] = -1e300; }
-        for (int base = 0; base < n_atoms; base += 512) {
-            const int m = n_atoms - base < 512 ? n_atoms - base : 512;
-            if (cudaMemcpyAsync(buf, d_pos + 3 * (size_t)base, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, s) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
+        if (cudaMemsetAsync(S->ext, 0, sizeof(S->ext), s) != cudaSuccess) return HD_ERR_CUDA;
+        for (int a = 0; a < 3; ++a)
+            if (cudaMemsetAsync(&S->ext[2 * a], 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
                 return HD_ERR_CUDA;
-            for (int k = 0; k < m; ++k)
-                for (int a = 0; a < 3; ++a) {
-                    mn[a] = buf[3 * k + a] < mn[a] ? buf[3 * k + a] : mn[a];
-                    mx[a] = buf[3 * k + a] > mx[a] ? buf[3 * k + a] : mx[a];
-                }
+        k_s_extent<<<(n_atoms + 255) / 256, 256, 0, s>>>(S, d_pos, n_atoms);
+        unsigned long long e[6];
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(e, S->ext, sizeof e, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HD_ERR_CUDA;
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = ord_value(e[2 * a]);
+            mx[a] = ord_value(e[2 * a + 1]);
+            if (!std::isfinite(mn[a]) || !std::isfinite(mx[a])) return HD_ERR_NUMERIC;
         }
     }
     long long ncell = 1;
@@ -210,9 +247,10 @@ extern "C" hd_status hd_nlist_static(const double *d_pos, int n_atoms, const dou
             G.origin[a] = 0.5 * (mn[a] + mx[a]);
             G.scale[a] = 4294967296.0 / span;
             G.lsb[a] = (float)(span / 4294967296.0);
-            G.w[a] = rl * (1.0 + 1e-4);
+            const double w = rl * (1.0 + 1e-4);
+            G.inv_w[a] = 1.0 / w;
             G.lo[a] = mn[a] - 1.0;
-            G.nc[a] = (int)std::ceil((mx[a] + 1.0 - G.lo[a]) / G.w[a]);
+            G.nc[a] = (int)std::ceil((mx[a] + 1.0 - G.lo[a]) / w);
             if (G.nc[a] < 1) G.nc[a] = 1;
         } else {
             G.nc[a] = 1;

@@ -24,8 +24,8 @@ HD_DRIVER_AUTO, HD_DRIVER_KERNELS, HD_DRIVER_PERSISTENT = 0, 1, 2
  F_ENERGY) = range(11)
 OBS_FIELDS = ["step", "t_md", "t_h", "V", "K", "dV", "sigma", "d", "F_R", "x_T", "y_T", "z_T",
               "n_rebuild", "boost", "q_iter", "q_fmax", "G", "fbody_x", "fbody_y", "fbody_z",
-              "vbody_x", "vbody_y", "vbody_z", "q_disp"]
-OBS_LEN = 24
+              "vbody_x", "vbody_y", "vbody_z", "q_disp", "n_dv_zero", "n_dv_band", "n_dv_max", "q_conv"]
+OBS_LEN = 28
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_NOMEM", 4: "HD_ERR_NUMERIC",
                 5: "HD_ERR_TIMEOUT", 6: "HD_ERR_STATE", 7: "HD_ERR_UNIMPLEMENTED", 8: "HD_ERR_OVERFLOW"}
 
@@ -278,10 +278,19 @@ class Batch:
 
     def quench(self, method=1, ftol=1e-6, max_iter=20000, step_size=None, theta=0.5, adopt=0):
         if step_size is None:
-            step_size = 0.002 if method == 0 else 0.01
+            step_size = 0.002 if method == 0 else 0.005
         flags = np.zeros(self.n_rep, dtype=np.int32)
         self._ck(hd_quench(self.ctx, method, ftol, max_iter, step_size, theta, adopt, flags))
+        self.last_flags = flags
         return flags
+
+    def qstats(self):
+        """Iterations (mean), largest final force, converged fraction and the
+        number of flagged replicas of the last quench."""
+        ob = self.obs()
+        return {"iters": float(ob[:, 14].mean()), "iters_max": int(ob[:, 14].max()), "fmax": float(ob[:, 15].max()),
+                "converged": float(ob[:, 27].mean()),
+                "flagged": int(getattr(self, "last_flags", np.zeros(1)).sum())}
 
     def _read(self, field, r, shape, dtype):
         out = np.empty(shape, dtype=dtype)

@@ -2,12 +2,13 @@
 
 Test infrastructure only: replicas step and quench in parallel through the
 oracle's OpenMP batch calls.  adopt follows hd_quench (0 keep r_O, 1 take
-the quenched positions of flagged replicas, 2 of every replica), and
+the quenched positions of flagged replicas, 2 of every replica; only a
+quench that reached ftol is taken), and
 set_bias follows hd_set_bias (rows of DeltaV_max, sigma_L, sigma_U, m).
 """
 import numpy as np
 
-OBS_LEN = 24
+OBS_LEN = 28
 
 
 class OracleBatch:
@@ -29,11 +30,12 @@ class OracleBatch:
         return ob
 
     def quench(self, method=1, ftol=1e-4, max_iter=2000, theta=0.5, adopt=0, step_size=None):
-        self.xq, _, _ = self.O.quench_batch(self.o, method=method, ftol=ftol, max_iter=max_iter,
-                                            step_size=step_size)
+        self.xq, _, fmax = self.O.quench_batch(self.o, method=method, ftol=ftol, max_iter=max_iter,
+                                               step_size=step_size)
         flags = np.array([int(o.transition(x, theta)[0]) for o, x in zip(self.o, self.xq)], dtype=np.int32)
         for k, o in enumerate(self.o):
-            if adopt == 2 or (adopt == 1 and flags[k]):
+            # as hd_quench: only a converged quench becomes r_O
+            if fmax[k] < ftol and (adopt == 2 or (adopt == 1 and flags[k])):
                 o.xo[...] = self.xq[k]
                 o.refresh()
         return flags

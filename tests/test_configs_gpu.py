@@ -1,4 +1,4 @@
-"""Full-size GPU parity on the two largest synthetic batches, sampled.
+"""Full-size GPU parity on the synthetic batches, sampled, with the bias on.
 
 * The uneven batch: 192 replicas drawn from seed 4 (2-D with 400-4,000 atoms
   and 3-D with 5,000-40,000 atoms, log-uniform sizes, T in [0.05, 0.15]),
@@ -7,21 +7,23 @@
   positions, about 5.36M atoms, stepped by the per-phase kernels.
 
 For sampled replicas the lists must equal the oracle's bit for bit, the
-split-form forces must be within 1e-5 RMS relative, the Maxwell-Boltzmann
-draws within 1e-6, and positions after 10 steps within 1e-4 of the oracle's.
+split-form forces must be within 1e-5 RMS relative (spec bound for the
+FP32 path), and the Maxwell-Boltzmann draws within 1e-6.  Then 100 steps run
+with the slope bias (Eq. 14) inside its band: each sampled replica's band is
+the 10%-90% range of sigma over an unbiased oracle pre-run of the same 100
+steps, so DeltaV moves between 0 and DeltaV_max during the run.  After the
+100 steps, DeltaV and sigma must be within 1e-6 relative of the oracle's
+(DeltaV with the sigma error pushed through Eq. 14 where the band is steep)
+and the increment of the boosted clock (Eq. 3) within 1e-6 relative.
 
-Known gap: the split form holds positions on a 32-bit fixed-point grid over
-the periodic length L, so its pair separations carry an error of order
-L/2^32.  The 1e-5 force bound holds up to L of about 150 sigma; the longest
-2-D strips of the uneven batch (up to 545 sigma, 3,925 atoms) reach 3.3e-5.
-Those strips are checked for lists and trajectories here and held to the
-force bound in an expected-failure test until the grid gets sub-unit bits.
-
-The bias band is placed far above every slope (sigma_L = 1e9), so DeltaV = 0
-and the sampled trajectories are plain Langevin MD with t_h = t_md.
+The longest 2-D strip of the uneven batch (545 sigma, 3,925 atoms) is held to
+the force bound on its own: positions there sit on a fixed-point grid of
+L / 2^36, fine enough for the bound at any box length.
 """
 import numpy as np
 import pytest
+
+from bandtools import run_band_prerun, sampled_bias_check
 
 pytestmark = pytest.mark.gpu
 
@@ -40,12 +42,7 @@ def rms_rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
 
 
-def _bias_off(reps):
-    for r in reps:
-        r.sig_lo, r.sig_hi = 1e9, 2e9
-
-
-def _check_sampled(b, oracle_mod, reps, p, sample, run_k, lists_only=()):
+def _check_initial(b, oracle_mod, reps, p, sample, lists_only=()):
     for k in list(sample) + list(lists_only):
         o = oracle_mod.OracleReplica(reps[k], p, draw_velocities=True)
         o.nlist_cells()
@@ -55,36 +52,28 @@ def _check_sampled(b, oracle_mod, reps, p, sample, run_k, lists_only=()):
         assert np.abs(b.velocities(k) - o.v).max() < 1e-6
         if k in sample:
             assert rms_rel(b.forces(k), o.f_lj) <= 1e-5
-    b.step(10)
-    ob = b.obs()
-    assert np.array_equal(ob[:, 0], np.full(len(reps), 10.0))
-    np.testing.assert_allclose(ob[:, 2], ob[:, 1], rtol=1e-12)        # boost 1: t_h = t_md
-    for k in run_k:
-        o = oracle_mod.OracleReplica(reps[k], p, draw_velocities=True)
-        o.run(10)
-        assert np.abs(b.positions(k) - o.x).max() < 1e-4
 
 
 def test_uneven_192_in_one_persistent_launch(hd, oracle_mod):
     from paper_0909_5215_gb300 import model as M
     reps, p = M.uneven_batch(n_rep=192, seed=4, prec=1)
-    _bias_off(reps)
     ns = np.array([r.n for r in reps])
     dims = np.array([r.dim for r in reps])
+    i2, i3 = np.nonzero(dims == 2)[0], np.nonzero(dims == 3)[0]
+    longest2 = int(i2[np.argmax(ns[i2])])
+    sample = [int(i2[np.argmin(ns[i2])]), longest2, int(i3[np.argmin(ns[i3])]), int(i3[np.argmax(ns[i3])])]
+    run_band_prerun(oracle_mod, reps, p, sample, steps=100)
     b = hd.Batch(reps, p, driver=hd.HD_DRIVER_PERSISTENT)
     assert b.info()["driver"] == hd.HD_DRIVER_PERSISTENT
-    box = np.array([r.box[0] for r in reps])
-    i2, i3 = np.nonzero(dims == 2)[0], np.nonzero(dims == 3)[0]
-    short2 = i2[box[i2] <= 150.0]
-    longest2 = int(i2[np.argmax(ns[i2])])
-    sample = [int(i2[np.argmin(ns[i2])]), int(short2[np.argmax(ns[short2])]),
-              int(i3[np.argmin(ns[i3])]), int(i3[np.argmax(ns[i3])])]
-    _check_sampled(b, oracle_mod, reps, p, sample, run_k=[longest2, sample[2]], lists_only=[longest2])
+    _check_initial(b, oracle_mod, reps, p, sample)
+    report = sampled_bias_check(b, oracle_mod, reps, p, sample, steps=100)
+    print("\n".join(report))
     b.close()
 
 
-@pytest.mark.xfail(strict=False, reason="split-form positions on a 32-bit grid over L: ~3e-5 at L = 545 sigma")
 def test_split_forces_on_longest_2d_strip(hd, oracle_mod):
+    """The 545-sigma strip: forces at the lattice and after 200 thermal steps
+    within the 1e-5 RMS bound of the FP32 path."""
     from paper_0909_5215_gb300 import model as M
     r = M.afm2d(n_cols=486, eps=M.PAPER_EPS_2D)
     p = M.Params(prec=1, bias_on=0)
@@ -93,6 +82,10 @@ def test_split_forces_on_longest_2d_strip(hd, oracle_mod):
     o.nlist_cells()
     try:
         assert rms_rel(b.forces(0), o.f_lj) <= 1e-5
+        b.step(200)
+        o.run(200)
+        assert rms_rel(b.forces(0), o.f_lj) <= 1e-5
+        assert np.abs(b.positions(0) - o.x).max() < 1e-4
     finally:
         b.close()
 
@@ -100,7 +93,12 @@ def test_split_forces_on_longest_2d_strip(hd, oracle_mod):
 def test_large_3d_batch_sampled(hd, oracle_mod):
     from paper_0909_5215_gb300 import model as M
     reps, p = M.afm3d_large(n_rep=32, prec=1)
-    _bias_off(reps)
+    sample = [0, 17, 31]
+    run_band_prerun(oracle_mod, reps, p, [17], steps=60)
+    for r in reps:
+        r.sig_lo, r.sig_hi = reps[17].sig_lo, reps[17].sig_hi
     b = hd.Batch(reps, p, driver=hd.HD_DRIVER_KERNELS)
-    _check_sampled(b, oracle_mod, reps, p, [0, 31], run_k=[17])
+    _check_initial(b, oracle_mod, reps, p, [0, 31])
+    report = sampled_bias_check(b, oracle_mod, reps, p, sample, steps=60)
+    print("\n".join(report))
     b.close()

@@ -170,7 +170,7 @@ def test_trajectory_100_steps(hd, oracle_mod, states, prec):
         assert ob["step"] == o.s.step
         assert ob["t_md"] == pytest.approx(o.s.t_md, rel=1e-15)
         if prec == 0:
-            assert ob["t_h"] == pytest.approx(o.s.t_h, rel=TOL_DV[prec])
+            assert ob["t_h"] - reps[k].t_h0 == pytest.approx(o.s.t_h - reps[k].t_h0, rel=TOL_DV[prec])
         assert abs(ob["dV"] - o.s.dV) <= dv_bound(o, prec) * (1 if prec == 0 else 30)
         xtol = 1e-9 if prec == 0 else 1e-4
         assert np.abs(b.positions(k) - o.x).max() < xtol
@@ -285,12 +285,14 @@ def test_escaping_atom_is_reported(hd, oracle_mod, states):
 
 
 def test_full_size_3d_batch_sampled(hd, oracle_mod):
-    """The 24x24x6-cell slab with a radius-6 tip, 64 slider positions: lists and
-    forces of sampled replicas equal the oracle's, after a few steps too."""
+    """The 24x24x6-cell slab with a radius-6 tip, 64 slider positions, bias on
+    with its band inside the slopes the run visits: lists and forces of sampled
+    replicas equal the oracle's, and after 100 steps DeltaV, sigma and the
+    boosted-clock increments agree within 1e-6."""
+    from bandtools import run_band_prerun, sampled_bias_check
     from paper_0909_5215_gb300 import model as M
     reps, p = M.afm3d_hyper(n_rep=64, prec=1)
-    for r in reps:
-        r.sig_lo, r.sig_hi = 1e9, 2e9       # bias inactive: sigma far below sigma_L
+    run_band_prerun(oracle_mod, reps, p, [37], steps=100)
     b = hd.Batch(reps, p)
     for k in (0, 37, 63):
         o = oracle_mod.OracleReplica(reps[k], p, draw_velocities=True)
@@ -299,10 +301,7 @@ def test_full_size_3d_batch_sampled(hd, oracle_mod):
         assert rms_rel(b.forces(k), o.f_lj) <= 1e-5
         v = b.velocities(k)
         assert np.abs(v - o.v).max() < 1e-6
-    b.step(10)
-    o = oracle_mod.OracleReplica(reps[37], p, draw_velocities=True)
-    o.run(10)
-    assert np.abs(b.positions(37) - o.x).max() < 1e-4
+    print("\n".join(sampled_bias_check(b, oracle_mod, reps, p, [0, 37, 63], steps=100)))
     b.close()
 
 
@@ -338,18 +337,60 @@ def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_stat
     for k, o in enumerate(ors):
         ob = b.obs(k)
         assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12)
+    th0 = [o.s.t_h for o in ors]
     b.step(100)
     report = []
     for k, o in enumerate(ors):
         o.run(100)
         ob = b.obs(k)
-        report.append("replica %d (dim %d): rel err t_h %.2e, dV %.2e, sigma %.2e" % (
-            k, workload_states[k].dim, abs(ob["t_h"] / o.s.t_h - 1), abs(ob["dV"] / o.s.dV - 1),
-            abs(ob["sigma"] / o.s.sigma - 1)))
+        report.append("replica %d (dim %d): rel err of the t_h increment %.2e, dV %.2e, sigma %.2e" % (
+            k, workload_states[k].dim, abs((ob["t_h"] - th0[k]) / (o.s.t_h - th0[k]) - 1),
+            abs(ob["dV"] / o.s.dV - 1), abs(ob["sigma"] / o.s.sigma - 1)))
     print("\n".join(report))
     for k, o in enumerate(ors):
         ob = b.obs(k)
-        assert ob["t_h"] == pytest.approx(o.s.t_h, rel=1e-6), report
+        assert ob["t_h"] - th0[k] == pytest.approx(o.s.t_h - th0[k], rel=1e-6), report
         assert ob["dV"] == pytest.approx(o.s.dV, rel=1e-6, abs=1e-12), report
         assert ob["sigma"] == pytest.approx(o.s.sigma, rel=1e-6), report
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_quench_fire_3d_workload_model(hd, oracle_mod, workload_states, prec):
+    """FIRE on the 14,272-atom 3-D model from a thermal state, to 1e-6 (FP64)
+    or 1e-4 (split): both converge, find the same minimum, and agree on the
+    transition test."""
+    st = workload_states[1]
+    p = _params(prec=prec, bias_on=1)
+    b = hd.Batch([st], p)
+    ftol = 1e-6 if prec == 0 else 1e-4
+    flags = b.quench(method=1, ftol=ftol, max_iter=20000, step_size=0.005, theta=0.5, adopt=0)
+    o = oracle_mod.OracleReplica(st, p)
+    xq, it, fm = o.quench(method=1, ftol=ftol, max_iter=20000, step_size=0.005)
+    ob = b.obs(0)
+    print("GPU %d iterations, fmax %.2e; oracle %d iterations, fmax %.2e" % (ob["q_iter"], ob["q_fmax"], it, fm))
+    assert fm < ftol and ob["q_fmax"] < ftol and ob["q_conv"] == 1.0
+    assert flags[0] == int(o.transition(xq, 0.5)[0])
+    assert np.abs(b.qpos(0) - xq).max() < (1e-4 if prec == 0 else 2e-3)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_quench_sd_3d_workload_model(hd, oracle_mod, workload_states, prec):
+    """Steepest descent on the 14,272-atom 3-D model: 300 iterations of the same
+    step give the same positions (the iteration is contractive, so the FP32
+    forces of the split form stay within their own error)."""
+    st = workload_states[1]
+    p = _params(prec=prec, bias_on=1)
+    b = hd.Batch([st], p)
+    b.quench(method=0, ftol=1e-12, max_iter=300, step_size=0.002, theta=0.5, adopt=0)
+    o = oracle_mod.OracleReplica(st, p)
+    xq, it, fm = o.quench(method=0, ftol=1e-12, max_iter=300, step_size=0.002)
+    ob = b.obs(0)
+    assert ob["q_iter"] == it == 300 and ob["q_conv"] == 0.0
+    assert ob["q_fmax"] == pytest.approx(fm, rel=1e-9 if prec == 0 else 1e-3)
+    assert np.abs(b.qpos(0) - xq).max() < (1e-9 if prec == 0 else 1e-5)
+    # an unconverged quench never becomes r_O
+    b.quench(method=0, ftol=1e-12, max_iter=50, step_size=0.002, theta=0.0, adopt=2)
+    assert np.array_equal(b.ref(0), st.pos_ref)
     b.close()
