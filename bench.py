@@ -155,7 +155,7 @@ def prepare_batch(reps, params, driver, block, split, setup_md=1000):
     b.tuned = tuned
     # seed r_O with the quenched lattice (converged: only a converged quench is
     # adopted), equilibrate, calibrate the bias band around that r_O
-    b.quench(method=1, ftol=1e-4 if split else 1e-6, max_iter=20000, step_size=QSTEP, theta=1e30, adopt=2)
+    b.quench(method=1, ftol=1e-3 if split else 1e-6, max_iter=20000, step_size=QSTEP, theta=1e30, adopt=2)
     ob = b.obs()
     b.seed_quench = {"converged": int(ob[:, 27].sum()), "of": len(reps), "iters_max": int(ob[:, 14].max()),
                      "fmax_max": float(ob[:, 15].max())}

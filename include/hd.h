@@ -96,6 +96,24 @@ typedef struct {
     double eps[2][2], sig[2][2];   /* LJ eps_ab, sigma_ab of Eq. 9, by type           */
     double t_h0, t_md0;        /* initial boosted and MD clocks (resume)              */
     int64_t step0;             /* initial step counter (Philox; resume)               */
+    double v_slide;            /* continuous sliding (Sec. 3.1.1, method 1): the slider
+                                  moves along x at this velocity, x_S = slider[0] +
+                                  k (v_slide dt) for a configuration k steps after the
+                                  slider was set; 0: stepped sliding, x_S fixed       */
+    int n_bonds;               /* harmonic bonds of Eq. 12 (Sec. 3.2.1): k_bond (r -
+                                  r_bond)^2 / 2 between the atom pairs of bonds; with
+                                  n_bonds > 0 tip-tip pairs (type 1 with type 1) have
+                                  no LJ term.  0: every pair is LJ                    */
+    int pad2_;
+    const int32_t *bonds;      /* [n_bonds][2] input atom indices i != j, or NULL     */
+    double k_bond, r_bond;     /* bond stiffness and rest length (paper: 57.2, 1.12)  */
+    int nhc_len;               /* Nose-Hoover chain (Sec. 3.1.1) of this length (1..8)
+                                  on the mobile atoms in place of the Langevin noise
+                                  (gamma unused); 0: Langevin.  The chain starts at
+                                  rest; masses Q_1 = N_f kT tau^2, Q_j = kT tau^2 with
+                                  N_f = dim x mobile atoms                           */
+    int pad3_;
+    double nhc_tau;            /* chain period tau                                    */
 } hd_replica_desc;
 
 typedef struct {
@@ -122,11 +140,12 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p,
                     void *d_workspace, size_t ws_bytes, void *cuda_stream, hd_ctx **out);
 
 /* Move the sliders: slider[2*r], slider[2*r+1] = (x_S, y_S) of replica r
- * (stepped sliding, Sec. 2.3 and Fig. 1).  If requench_ref is non-zero, each
+ * (stepped sliding, Sec. 2.3 and Fig. 1); a replica with v_slide != 0 moves
+ * on from there at v_slide, counting steps from the current configuration.  If requench_ref is non-zero, each
  * replica is then quenched (FIRE from dt0 = 0.005, at most 20000 steps, to
- * ftol 1e-6 in the FP64 form and 1e-4 in the split form, whose FP32 pair
- * forces do not resolve the rigid body's summed force below that) and r_O
- * is set to the result where the quench converged (HD_OBS_QCONV). */
+ * ftol 1e-6 in the FP64 form and 1e-3 in the split form, whose FP32 pair
+ * forces do not resolve the rigid body's summed force much below that) and
+ * r_O is set to the result where the quench converged (HD_OBS_QCONV). */
 hd_status hd_set_slider(hd_ctx *ctx, const double *slider, int requench_ref);
 
 /* Replace the bias parameters of Eq. 14: bias[4*r .. 4*r+3] =
@@ -177,7 +196,9 @@ enum {
     HD_OBS_NDV_BAND = 25,      /* ... with 0 < DeltaV < DeltaV_max                    */
     HD_OBS_NDV_MAX = 26,       /* ... with DeltaV = DeltaV_max (sigma >= sigma_U)      */
     HD_OBS_QCONV = 27,         /* 1 if the last quench reached ftol, else 0            */
-    HD_OBS_LEN = 28
+    HD_OBS_XS = 28,            /* slider x_S of the current configuration             */
+    HD_OBS_NHC_E = 29,         /* chain energy sum Q v^2/2 + N_f kT xi_1 + kT sum xi_j */
+    HD_OBS_LEN = 32
 };
 
 hd_status hd_read(hd_ctx *ctx, int field, int replica, void *h_dst, size_t bytes);

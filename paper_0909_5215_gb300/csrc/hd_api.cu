@@ -30,13 +30,15 @@ struct Plan {
     // initial configuration, z then y then x, input order inside a cell);
     // slot_orig[global slot] = the atom's index in the replica's input arrays
     std::vector<int> slot_orig;
+    // bond partners per slot (Eq. 12), CSR over all replicas' slots
+    std::vector<int> bond_off, bond_j;
     size_t bytes = 0;
     // offsets
     size_t o_rep, o_st, o_sc, o_trep, o_tstart, o_tn, o_part, o_qpart, o_kpart;
     size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
     size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff;
-    size_t o_ctarep, o_pgfirst, o_pgcount;
+    size_t o_ctarep, o_pgfirst, o_pgcount, o_boff, o_bj;
 };
 
 size_t take(size_t &cur, size_t bytes) {
@@ -51,6 +53,18 @@ bool valid_desc(const hd_replica_desc &d, std::string &why) {
     if (d.n_atoms <= 0 || !d.pos || !d.role || !d.type) { why = "empty replica or NULL arrays"; return false; }
     if (d.kT <= 0.0 || d.gamma < 0.0) { why = "kT must be > 0 and gamma >= 0"; return false; }
     if (d.m_exp < 1) { why = "m_exp must be >= 1"; return false; }
+    if (!std::isfinite(d.v_slide)) { why = "v_slide must be finite"; return false; }
+    if (d.n_bonds < 0 || (d.n_bonds > 0 && !d.bonds)) { why = "n_bonds < 0 or NULL bonds"; return false; }
+    if (d.nhc_len < 0 || d.nhc_len > 8) { why = "nhc_len must be in [0, 8]"; return false; }
+    if (d.nhc_len > 0 && !(d.nhc_tau > 0.0 && std::isfinite(d.nhc_tau))) { why = "nhc_tau must be > 0"; return false; }
+    if (d.n_bonds > 0 && !(d.k_bond >= 0.0 && std::isfinite(d.k_bond) && d.r_bond > 0.0 && std::isfinite(d.r_bond))) {
+        why = "k_bond must be >= 0 and r_bond > 0";
+        return false;
+    }
+    for (int b = 0; b < d.n_bonds; ++b) {
+        const int i = d.bonds[2 * b], j = d.bonds[2 * b + 1];
+        if (i < 0 || j < 0 || i >= d.n_atoms || j >= d.n_atoms || i == j) { why = "bond with a bad atom index"; return false; }
+    }
     for (int a = 0; a < d.dim - 1; ++a)
         if (!d.periodic[a] || !(d.box[a] > 0.0)) {
             snprintf(b, sizeof b, "in-plane axis %d must be periodic with a positive length", a);
@@ -215,6 +229,8 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
         R.fnormal = d.f_normal;
         R.slider[0] = d.slider[0];
         R.slider[1] = d.slider[1];
+        R.v_slide = d.v_slide;
+        R.slide_step0 = d.step0;
         R.dvmax = d.dvmax;
         R.sig_lo = d.sig_lo;
         R.sig_hi = d.sig_hi;
@@ -231,9 +247,41 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                 const double r0sq = std::cbrt(2.0) * sig * sig;   // LJ minimum 2^(1/6) sigma, squared
                 R.r0sq_hi[a][b] = (float)r0sq;
                 R.r0sq_lo[a][b] = (float)(r0sq - (double)R.r0sq_hi[a][b]);
+                R.eps24f[a][b] = (float)(24.0 * eps);
+                R.eps96f[a][b] = (float)(96.0 * eps);
+                // the pair sweep takes the exact r^2 where |r_0^2 - r^2| < r^2 / 4,
+                // i.e. r^2 < (4/3) r_0^2; class A of the list holds the pairs within
+                // that radius plus 0.1 sigma at build time
+                const double rA = std::sqrt(r0sq * 4.0 / 3.0) + 0.1 * sig;
+                R.rA2f = std::max(R.rA2f, (float)(rA * rA));
             }
         R.kr_n = nrig > 0 ? d.k_spring / nrig : 0.0;
         R.kr_nf = (float)R.kr_n;
+        // Nose-Hoover chain masses: Q_1 = N_f kT tau^2, Q_j = kT tau^2
+        R.nhc_len = d.nhc_len;
+        if (d.nhc_len > 0) {
+            int nmob = 0;
+            for (int i = 0; i < d.n_atoms; ++i) nmob += d.role[i] == 1;
+            R.nhc_nf = (double)(d.dim * nmob);
+            const double t2 = d.nhc_tau * d.nhc_tau;
+            for (int j = 0; j < d.nhc_len; ++j) R.nhc_Q[j] = (j == 0 ? R.nhc_nf : 1.0) * d.kT * t2;
+        }
+        // Eq. 12 bonds: with any bond, tip-tip pairs have no LJ term (zero
+        // eps_tt and shift; the bond table carries their interaction)
+        R.nbond = d.n_bonds;
+        if (d.n_bonds > 0) {
+            R.kbond = d.k_bond;
+            R.rbond = d.r_bond;
+            R.kbondf = (float)d.k_bond;
+            R.rbond_hi = (float)d.r_bond;
+            R.rbond_lo = (float)(d.r_bond - (double)R.rbond_hi);
+            R.eps[1][1] = 0.0;
+            R.shift[1][1] = 0.0;
+            R.epsf[1][1] = 0.f;
+            R.shiftf[1][1] = 0.f;
+            R.eps24f[1][1] = 0.f;
+            R.eps96f[1][1] = 0.f;
+        }
         P.rep[r] = R;
         for (int k = 0; k < R.ntile; ++k) {
             P.tile_rep.push_back(r);
@@ -248,6 +296,27 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.natom = (int)natom;
     P.ntile = (int)ntile;
     P.ncell = (int)ncell;
+    {
+        // bond partners per slot, both directions, in the replicas' storage order
+        std::vector<int> deg(P.natom, 0), slot_of;
+        std::vector<std::vector<int>> part(P.natom);
+        for (int r = 0; r < n_rep; ++r) {
+            const hd_replica_desc &d = reps[r];
+            if (d.n_bonds <= 0) continue;
+            const int a0 = P.rep[r].atom0;
+            slot_of.assign(d.n_atoms, 0);
+            for (int sl = 0; sl < d.n_atoms; ++sl) slot_of[P.slot_orig[a0 + sl]] = a0 + sl;
+            for (int b = 0; b < d.n_bonds; ++b) {
+                const int i = slot_of[d.bonds[2 * b]], j = slot_of[d.bonds[2 * b + 1]];
+                part[i].push_back(j);
+                part[j].push_back(i);
+            }
+        }
+        P.bond_off.assign(P.natom + 1, 0);
+        for (int i = 0; i < P.natom; ++i) P.bond_off[i + 1] = P.bond_off[i] + (int)part[i].size();
+        P.bond_j.clear();
+        for (int i = 0; i < P.natom; ++i) P.bond_j.insert(P.bond_j.end(), part[i].begin(), part[i].end());
+    }
     P.cell_cap = p->cell_cap > 0 ? p->cell_cap : ((2 * max_occ + 8 + 7) / 8) * 8;
     // layout
     const size_t N = P.natom, T = P.ntile, R = P.nrep;
@@ -292,6 +361,8 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_ctarep = take(cur, T * 4);       // at most one CTA per tile
     P.o_pgfirst = take(cur, R * 4);
     P.o_pgcount = take(cur, R * 4);
+    P.o_boff = take(cur, (N + 1) * 4);
+    P.o_bj = take(cur, std::max<size_t>(1, P.bond_j.size()) * 4);
     P.bytes = (cur + ALIGN - 1) / ALIGN * ALIGN;
     return true;
 }
@@ -313,6 +384,8 @@ struct hd_ctx {
     bool persist_graph_ok = true;
     std::vector<double> qdisp;
     std::vector<int> qflag, qconv;
+    long long steps_done = 0;             // hd_step advances every replica alike
+    std::vector<long long> step0;
     long long h2d = 0, d2h = 0;
     // timing: events recorded around phases; harvested at hd_timing / next step
     int timing = 0;
@@ -468,6 +541,8 @@ void fill_dev(hd_ctx *c) {
     if (const char *e = getenv("HD_TEST_SKIP_ARRIVE")) D.fault_rep = atoi(e);
     D.pg_first = at<int>(b, P.o_pgfirst);
     D.pg_count = at<int>(b, P.o_pgcount);
+    D.bond_off = at<int>(b, P.o_boff);
+    D.bond_j = at<int>(b, P.o_bj);
     D.nl_pow2 = 32;
     while (D.nl_pow2 < P.maxnb) D.nl_pow2 <<= 1;
     {
@@ -538,16 +613,31 @@ hd_status upload_reps(hd_ctx *c) {
 
 // Kernels of one BAOAB step after the opening half (list, pair, scalars, update).
 void queue_step(hd_ctx *c, int mode, std::vector<hd_ctx::Span> *sink) {
+    // per-atom energies are observables only: computed on the last step of a call
+    const bool last = !(mode & MODE_OPEN);
     { Timed t(c, sink, T_REBUILD); launch_rebuild(c->D, c->s); }
-    { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, c->s); }
+    { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, last, c->s); }
     { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, mode, c->s); }
-    { Timed t(c, sink, T_UPDATE); launch_update(c->D, mode, c->s); }
-    c->launches += 8;
+    if (!c->D.any_nhc) {
+        { Timed t(c, sink, T_UPDATE); launch_update(c->D, mode, c->s); }
+        c->launches += 8;
+        return;
+    }
+    // a Nose-Hoover chain needs the kinetic sums of the closing kick before
+    // the velocities are scaled, so the update splits around the chain
+    { Timed t(c, sink, T_UPDATE); launch_update(c->D, MODE_CLOSE, c->s); }
+    launch_nhc(c->D, mode, c->s);
+    { Timed t(c, sink, T_UPDATE); launch_update(c->D, (mode & MODE_OPEN) ? (MODE_OPEN | MODE_NHC) : MODE_SCALE, c->s); }
+    c->launches += 10;
 }
 
 void queue_steps(hd_ctx *c, int n, std::vector<hd_ctx::Span> *sink) {
     { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, MODE_OPEN, c->s); }
-    { Timed t(c, sink, T_UPDATE); launch_update(c->D, MODE_OPEN, c->s); }
+    if (c->D.any_nhc) {
+        launch_nhc(c->D, MODE_OPEN, c->s);
+        c->launches += 1;
+    }
+    { Timed t(c, sink, T_UPDATE); launch_update(c->D, c->D.any_nhc ? (MODE_OPEN | MODE_NHC) : MODE_OPEN, c->s); }
     c->launches += 2;
     for (int k = 1; k <= n; ++k) queue_step(c, k < n ? (MODE_CLOSE | MODE_OPEN) : MODE_CLOSE, sink);
 }
@@ -562,7 +652,7 @@ hd_status refresh_md(hd_ctx *c, bool relist) {
         c->launches += 5;
         CK(cudaStreamSynchronize(c->s));
     }
-    launch_pair(c->D, false, c->s);
+    launch_pair(c->D, false, true, c->s);
     launch_scalar(c->D, 0, c->s);
     c->launches += 2;
     CK(cudaGetLastError());
@@ -581,7 +671,7 @@ bool setup_persistent(hd_ctx *c) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (P.block > 128) return false;  // the persistent kernel is built for tiles of <= 128 atoms
-    const int bps = persist_blocks_per_sm(P.prec, P.block);
+    const int bps = persist_blocks_per_sm(c->D);
     const long long maxg = (long long)bps * nsm;
     if (!coop || bps <= 0 || P.nrep > maxg) return false;
     std::vector<double> w(P.nrep);
@@ -650,6 +740,10 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     fill_dev(c);
     set_scalars(c->D, p);
     set_scalars(c->Q, p);
+    CK(nl_configure(c->D));
+    c->D.any_nhc = 0;
+    for (int r = 0; r < n_rep; ++r) c->D.any_nhc |= reps[r].nhc_len > 0;
+    c->Q.any_nhc = c->D.any_nhc;
     Plan &P = c->P;
     const size_t N = P.natom;
     CK(cudaMemsetAsync(c->ws, 0, P.bytes, c->s));
@@ -697,21 +791,27 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     CK(cudaMemcpyAsync(c->D.xo, hxo.data(), N * sizeof(dbl4), cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->D.rec, hp.data(), N * sizeof(AtomRec), cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync((void *)c->D.orig, P.slot_orig.data(), N * 4, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync((void *)c->D.bond_off, P.bond_off.data(), (N + 1) * 4, cudaMemcpyHostToDevice, c->s));
+    if (!P.bond_j.empty())
+        CK(cudaMemcpyAsync((void *)c->D.bond_j, P.bond_j.data(), P.bond_j.size() * 4, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->ws + P.o_v, hv.data(), hv.size(), cudaMemcpyHostToDevice, c->s));
     int *d_draw = at<int>(c->ws, P.o_drawvel);
     CK(cudaMemcpyAsync(d_draw, draw.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->D.rebuild, two.data(), P.nrep * 4, cudaMemcpyHostToDevice, c->s));
     launch_init(c->D, d_draw, c->s);
     launch_rebuild(c->D, c->s);
-    launch_pair(c->D, false, c->s);
+    launch_pair(c->D, false, true, c->s);
     launch_scalar(c->D, 0, c->s);
     launch_update(c->D, MODE_KIN, c->s);  // kinetic energy of the initial velocities
+    launch_nhc(c->D, MODE_KIN, c->s);     // the chains start from it
     launch_obs(c->D, c->s);
-    c->launches += 10;
+    c->launches += 11;
     CK(cudaGetLastError());
     c->qdisp.assign(P.nrep, 0.0);
     c->qflag.assign(P.nrep, 0);
     c->qconv.assign(P.nrep, 0);
+    c->step0.resize(P.nrep);
+    for (int r = 0; r < P.nrep; ++r) c->step0[r] = reps[r].step0;
     if (p->driver == HD_DRIVER_PERSISTENT && setup_persistent(c)) c->driver = HD_DRIVER_PERSISTENT;
     return check_device(c);
 }
@@ -721,19 +821,20 @@ hd_status hd_set_slider(hd_ctx *c, const double *slider, int requench_ref) {
     if (c->status != HD_OK) return HD_ERR_STATE;
     if (!slider) return fail(c, HD_ERR_ARG, "NULL slider array");
     for (int r = 0; r < c->P.nrep; ++r) {
+        if (!std::isfinite(slider[2 * r]) || !std::isfinite(slider[2 * r + 1]))
+            return fail(c, HD_ERR_ARG, "replica %d: non-finite slider position", r);
         c->P.rep[r].slider[0] = slider[2 * r];
         c->P.rep[r].slider[1] = slider[2 * r + 1];
+        c->P.rep[r].slide_step0 = c->step0[r] + c->steps_done;   // a moving slider restarts from here
     }
-    // only the two slider words of each replica's settings block move
-    CK(cudaMemcpy2DAsync((char *)c->D.rep + offsetof(RepDev, slider), sizeof(RepDev), &c->P.rep[0].slider[0],
-                         sizeof(RepDev), 2 * sizeof(double), c->P.nrep, cudaMemcpyHostToDevice, c->s));
-    c->h2d += 16LL * c->P.nrep;
+    if (upload_reps(c) != HD_OK) return c->status;
     launch_scalar(c->D, 0, c->s);
     c->launches += 1;
     CK(cudaGetLastError());
-    // FIRE from dt0 = 0.005 (fastest on thermal LJ states); the split form's
-    // FP32 pair forces reach 1e-4 but not 1e-6 on the rigid body's sum
-    if (requench_ref) return hd_quench(c, 1, c->P.prec == HD_FP64 ? 1e-6 : 1e-4, 20000, 0.005, 1e300, 2, nullptr);
+    // FIRE from dt0 = 0.005 (fastest on thermal LJ states); the rigid body's
+    // force, a sum over its atoms' FP32 pair forces, levels off near 4e-4 in
+    // the split form, so that form quenches to 1e-3
+    if (requench_ref) return hd_quench(c, 1, c->P.prec == HD_FP64 ? 1e-6 : 1e-3, 20000, 0.005, 1e300, 2, nullptr);
     return HD_OK;
 }
 
@@ -760,6 +861,7 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     if (c->status != HD_OK) return HD_ERR_STATE;
     if (n_steps < 0) return fail(c, HD_ERR_ARG, "n_steps < 0");
     if (n_steps == 0) return HD_OK;
+    c->steps_done += n_steps;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(c->s, &cs));
     const bool can_graph = c->s != nullptr && cs == cudaStreamCaptureStatusNone;
@@ -833,7 +935,7 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     }
     CK(cudaGraphLaunch(it->second, c->s));
     if (c->timing) c->graph_pending.push_back(key);
-    c->launches += 2 + 8LL * n_steps;
+    c->launches += c->D.any_nhc ? 3 + 10LL * n_steps : 2 + 8LL * n_steps;
     return HD_OK;
 }
 
@@ -1053,6 +1155,13 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         o[HD_OBS_QDISP] = c->qdisp.empty() ? 0.0 : c->qdisp[replica];
         for (int a = 0; a < 3; ++a) o[HD_OBS_NDV_ZERO + a] = (double)S.n_dv[a];
         o[HD_OBS_QCONV] = c->qconv.empty() ? 0.0 : (double)c->qconv[replica];
+        o[HD_OBS_XS] = C.xS;
+        if (R.nhc_len > 0) {
+            double e = 0.0;
+            for (int j = 0; j < R.nhc_len; ++j)
+                e += 0.5 * R.nhc_Q[j] * S.nhc_v[j] * S.nhc_v[j] + (j == 0 ? R.nhc_nf : 1.0) * R.kT * S.nhc_xi[j];
+            o[HD_OBS_NHC_E] = e;
+        }
         return HD_OK;
     }
     default:

@@ -50,7 +50,11 @@ enum {
 };
 enum { QP_FMAX2 = 0, QP_P = 1, QP_VV = 2, QP_FF = 3, QP_FRIG = 4, QP_XRIG = 7, QP_PAD = 10 };
 
-enum { MODE_CLOSE = 1, MODE_OPEN = 2, MODE_KIN = 4 };  // KIN: kinetic energy only
+// KIN: kinetic energy only.  NHC: scale the mobile velocities by the chain's
+// factor before the opening kick and take no Langevin noise.  SCALE: only
+// scale the mobile velocities by the chain's factor (closing chain half step
+// of the last step of a call), kinetic energy after it.
+enum { MODE_CLOSE = 1, MODE_OPEN = 2, MODE_KIN = 4, MODE_NHC = 8, MODE_SCALE = 16 };
 enum { ROLE_FIXED = 0, ROLE_MOBILE = 1, ROLE_RIGID = 2 };
 
 // Per-atom record read by the pair sweep: fixed-point position (w = type |
@@ -66,6 +70,8 @@ struct RepDev {
     int nc[3], periodic[3];
     double L[3], invL[3];
     double kT, beta, c_ou, s_ou, kspring, fnormal, slider[2];
+    double v_slide;              // continuous sliding: x_S = slider[0] + (step - slide_step0) (v_slide dt)
+    long long slide_step0;       // step count of the configuration at which slider[0] was set
     double dvmax, sig_lo, sig_hi;
     double eps[2][2], sig2[2][2], shift[2][2];
     float epsf[2][2], sig2f[2][2], shiftf[2][2];
@@ -85,25 +91,36 @@ struct RepDev {
     float lsb_rel[3];            // (unit - fl32(unit)) / fl32(unit) per axis
     float pad2;
     float r0sq_hi[2][2], r0sq_lo[2][2];  // 2^(1/3) sigma_ab^2 (LJ minimum, squared) as hi + lo
+    float eps24f[2][2], eps96f[2][2];    // 24 eps_ab, 96 eps_ab
+    float rA2f;                  // list class A (first shell): FP32 r^2 below this at build time
+    float kbondf;                // Eq. 12 bonds: stiffness (FP32)
+    double kbond, rbond;         // Eq. 12 bonds: stiffness, rest length
+    float rbond_hi, rbond_lo;    // rest length as FP32 hi + lo
+    int nbond;                   // bonds of this replica (0: none; then every pair is LJ)
+    int nhc_len;                 // Nose-Hoover chain length (0: Langevin)
+    double nhc_nf, nhc_Q[8];     // chain: degrees of freedom, masses
 };
 
 struct RepState {
     double t_h, t_md, vbody[3], vbody_full[3], K;
     long long step, n_rebuild;
     long long n_dv[3];           // steps with DeltaV = 0, inside the band, at DeltaV_max
+    double nhc_xi[8], nhc_v[8];  // Nose-Hoover chain positions and velocities
+    double nhc_k2;               // sum of m v^2 over mobile atoms after the last chain half step
     // quench
     double q_dt, q_alpha, q_vb[3], q_fmax, q_disp;
     int q_npos, q_iter, q_done, q_flag;
 };
 
 struct Scal {
-    double d, sigma, dV, dVp, G, V, Vlj, xT[3], fbody[3], FR;
+    double d, sigma, dV, dVp, G, V, Vlj, xT[3], fbody[3], FR, xS;
     double ca, cb;
     double vb_mid[3], vb_new[3];
     long long step_cur;
     // quench scalars of the current iteration
     double q_fbody[3], q_mix, q_alpha, q_dt, q_vb[3];
     int q_zero, q_active;
+    double nhc_scale;            // chain: scale of the mobile velocities before the next kick
 };
 
 struct Dev {
@@ -132,8 +149,10 @@ struct Dev {
     int *rb_off;                 // [nrep + 1] compacted atom offsets of rebuilding replicas
     const int *cta_rep;          // persistent launch: replica of each CTA (-1: spare)
     const int *pg_first, *pg_count;  // persistent launch: first CTA and CTA count of each replica
+    const int *bond_off, *bond_j;    // per slot: bond partners (slots) in bond_j[bond_off[i] .. bond_off[i+1])
     int fault_rep;               // test hook (-1 off): a CTA of this replica skips one barrier arrival
     int nl_pow2, nl_grid;        // neighbour-row buffer (power of two >= maxnb), k_nlist CTAs
+    int any_nhc;                 // some replica runs a Nose-Hoover chain: the update splits around it
 };
 
 // ------------------------------------------------------------------ helpers
@@ -284,6 +303,14 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Slider x of the configuration reached after `step` steps: fixed (stepped
+// sliding, Sec. 2.3) or moving at v_slide (continuous sliding, Sec. 3.1.1),
+// written in closed form so that it does not accumulate rounding.
+__device__ __forceinline__ double slider_x(const RepDev &R, long long step, double dt) {
+    if (R.v_slide == 0.0) return R.slider[0];
+    return R.slider[0] + (double)(step - R.slide_step0) * (R.v_slide * dt);
 }
 
 // Eq. 14: value and derivative of DeltaV_1(sigma).

@@ -188,132 +188,182 @@ __global__ void k_cellsort(Dev D) {
     if (c < R.ncell) dev_cellsort_one(D, R, c);
 }
 
-// Prefix of the atom counts of the replicas whose rebuild flag is set:
-// rb_off[r] = first compacted index of replica r, rb_off[nrep] = total.
+// Prefix of the cell counts of the replicas whose rebuild flag is set:
+// rb_off[r] = first compacted cell of replica r, rb_off[nrep] = total.
 __global__ void k_rebuild_plan(Dev D) {
     if (threadIdx.x != 0) return;
     int tot = 0;
     for (int r = 0; r < D.nrep; ++r) {
         D.rb_off[r] = tot;
-        if (D.rebuild[r]) tot += D.rep[r].n;
+        if (D.rebuild[r]) tot += D.rep[r].ncell;
     }
     D.rb_off[D.nrep] = tot;
 }
 
 // Row i = every j != i whose FP64 minimum-image squared distance is below
-// (rc + skin)^2.  One warp per atom: the 27 (9 in 2-D) surrounding cells are
-// walked in ascending cell order, the lanes testing one cell's list at a time
-// (an FP32 test on the exact integer differences decides all but a thin band
-// around the radius, where the oracle's FP64 test is repeated operation for
-// operation), and accepted j are packed by ballot: those within the cutoff rc
-// at build time from the front of the row in candidate order, the skin shell
-// from the back, and the shell block is then moved down behind the inner
-// one.  Lanes of the pair sweep thus cross from inside to outside rc at
-// nearly the same k, and whole warps skip the tail of their rows.  The row
-// order is a deterministic function of the cell lists (sorted by
-// k_cellsort); reads return each row ascending in j.
-__device__ __forceinline__ void dev_nlist_atom(const Dev &D, int r, int i, int lane) {
-    const unsigned full = 0xffffffffu;
-    const int cap = D.maxnb;
+// (rc + skin)^2.  One CTA builds the rows of one cell's atoms.  It first
+// stages the candidates of the cell's stencil (the 27, or 9 in 2-D,
+// surrounding cells in ascending cell order, each cell's atoms ascending) in
+// shared memory: index and fixed-point position.  Then one warp per atom of
+// the cell walks the staged candidates 32 at a time.  An FP32 test on the
+// exact integer differences decides all but a thin band around the radius,
+// where the oracle's FP64 test is repeated operation for operation.  Each
+// accepted j gets a class, kept in shared memory:
+//   A (first shell) FP32 r^2 < rA^2, the pairs that can come within the
+//                   range where the pair sweep takes the exact r^2;
+//   B               the rest of the pairs within rc at build time;
+//   C (skin shell)  the rest of the row.
+// The row is then written as A | B | C, each block in candidate order, so the
+// lanes of the pair sweep leave the first shell, and later the cutoff, at
+// nearly the same k.  The row order is a deterministic function of the cell
+// lists (sorted by k_cellsort); reads return each row ascending in j.
+struct NlSmem {
+    int nst, tot, kc;
+    int cell[27], off[28];
+};
+
+__device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSmem &M, int4 *sp, int *sj,
+                                               unsigned char *scls) {
     const RepDev &R = D.rep[r];
-    const int4 pi = D.rec[i].p;
-    const dbl4 xi = D.x[i];
-    const int cid = D.cellid[i];
-    const int ci[3] = {cid & 1023, (cid >> 10) & 1023, (cid >> 20) & 1023};
-    int cs[3][3], ncs[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int nc = R.nc[a];
-        ncs[a] = 0;
-        if (nc == 1) {
-            cs[a][ncs[a]++] = 0;
-        } else {
-            // ascending: a periodic wrap puts nc-1 after 0 and 1
-            const int c0 = ci[a] - 1, c2 = ci[a] + 1;
-            if (R.periodic[a]) {
-                if (c0 < 0) { cs[a][0] = 0; cs[a][1] = 1; cs[a][2] = nc - 1; }
-                else if (c2 >= nc) { cs[a][0] = 0; cs[a][1] = nc - 2; cs[a][2] = nc - 1; }
-                else { cs[a][0] = c0; cs[a][1] = ci[a]; cs[a][2] = c2; }
-                ncs[a] = 3;
+    const int cell0 = R.cell0 + c;
+    const int m = min(D.cell_cnt[cell0], D.cell_cap);
+    if (m == 0) return;  // uniform: every thread reads the same count
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        const int ci[3] = {c % R.nc[0], (c / R.nc[0]) % R.nc[1], c / (R.nc[0] * R.nc[1])};
+        int cs[3][3], ncs[3];
+        for (int a = 0; a < 3; ++a) {
+            const int nc = R.nc[a];
+            ncs[a] = 0;
+            if (nc == 1) {
+                cs[a][ncs[a]++] = 0;
             } else {
-                if (c0 >= 0) cs[a][ncs[a]++] = c0;
-                cs[a][ncs[a]++] = ci[a];
-                if (c2 < nc) cs[a][ncs[a]++] = c2;
-            }
-        }
-    }
-    const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
-    const size_t stride = (size_t)D.natom;
-    int n_in = 0, n_sh = 0;
-    // cells in ascending order (x fastest), lanes over one cell's list at a time
-    for (int iz = 0; iz < ncs[2]; ++iz)
-        for (int iy = 0; iy < ncs[1]; ++iy)
-            for (int ix = 0; ix < ncs[0]; ++ix) {
-                const int cell = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
-                const int cnt = min(D.cell_cnt[cell], D.cell_cap);
-                const int *ca = D.cell_atoms + (size_t)cell * D.cell_cap;
-                for (int base = 0; base < cnt; base += 32) {
-                    const int c = base + lane;
-                    bool in = false, inner = false;
-                    int j = -1;
-                    if (c < cnt) {
-                        j = ca[c];
-                        if (j != i) {
-                            const int4 pj = D.rec[j].p;
-                            const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
-                            const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
-                            const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < D.rl2_lo_f) in = true;
-                            else if (r2 >= D.rl2_hi_f) in = false;
-                            else in = exact_r2(R, xi, D.x[j]) < D.rl2;
-                            inner = in && r2 < D.rc2_lo_f;
-                        }
-                    }
-                    const unsigned m = __ballot_sync(full, in);
-                    const unsigned mi = __ballot_sync(full, inner);
-                    if (in) {
-                        const unsigned below = (1u << lane) - 1u;
-                        const int pos = inner ? n_in + __popc(mi & below) : cap - 1 - (n_sh + __popc(m & ~mi & below));
-                        if (pos >= 0 && pos < cap) D.nbr[(size_t)pos * stride + i] = j;
-                    }
-                    n_in += __popc(mi);
-                    n_sh += __popc(m & ~mi);
+                // ascending: a periodic wrap puts nc-1 after 0 and 1
+                const int c0 = ci[a] - 1, c2 = ci[a] + 1;
+                if (R.periodic[a]) {
+                    if (c0 < 0) { cs[a][0] = 0; cs[a][1] = 1; cs[a][2] = nc - 1; }
+                    else if (c2 >= nc) { cs[a][0] = 0; cs[a][1] = nc - 2; cs[a][2] = nc - 1; }
+                    else { cs[a][0] = c0; cs[a][1] = ci[a]; cs[a][2] = c2; }
+                    ncs[a] = 3;
+                } else {
+                    if (c0 >= 0) cs[a][ncs[a]++] = c0;
+                    cs[a][ncs[a]++] = ci[a];
+                    if (c2 < nc) cs[a][ncs[a]++] = c2;
                 }
             }
-    const int n = n_in + n_sh;
-    // move the shell block [cap - n_sh, cap) down to [n_in, n); the target
-    // starts below the source, so chunks taken in ascending order, each read
-    // in full before it is written, never overwrite an unread entry
-    __syncwarp();
-    if (n < cap) {  // n == cap: already in place; n > cap: overflow, reported below
-        for (int b = 0; b < n_sh; b += 32) {
-            const int k = b + lane;
-            int v = 0;
-            if (k < n_sh) v = D.nbr[(size_t)(cap - n_sh + k) * stride + i];
-            __syncwarp();
-            if (k < n_sh) D.nbr[(size_t)(n_in + k) * stride + i] = v;
-            __syncwarp();
+        }
+        int k = 0, tot = 0;
+        for (int iz = 0; iz < ncs[2]; ++iz)
+            for (int iy = 0; iy < ncs[1]; ++iy)
+                for (int ix = 0; ix < ncs[0]; ++ix) {
+                    const int cc = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
+                    if (cc == cell0) M.kc = k;
+                    M.cell[k] = cc;
+                    M.off[k] = tot;
+                    tot += min(D.cell_cnt[cc], D.cell_cap);
+                    ++k;
+                }
+        M.off[k] = tot;
+        M.nst = k;
+        M.tot = tot;
+    }
+    __syncthreads();
+    // stage the stencil: warp q copies stencil cells q, q + nw, ...
+    for (int k = w; k < M.nst; k += nw) {
+        const int *ca = D.cell_atoms + (size_t)M.cell[k] * D.cell_cap;
+        const int o = M.off[k], n = M.off[k + 1] - o;
+        for (int t = lane; t < n; t += 32) {
+            const int j = ca[t];
+            sj[o + t] = j;
+            sp[o + t] = D.rec[j].p;
         }
     }
-    if (lane == 0) {
-        D.nnb[i] = min(n, cap);
-        if (n > cap) set_err(D, HD_ERR_OVERFLOW, i, r);
+    __syncthreads();
+    const int tot = M.tot, cap = D.maxnb;
+    const unsigned full = 0xffffffffu;
+    const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
+    const size_t stride = (size_t)D.natom;
+    unsigned char *cls = scls + (size_t)w * (27 * D.cell_cap);
+    for (int a = w; a < m; a += nw) {
+        const int slot = M.off[M.kc] + a;
+        const int i = sj[slot];
+        const int4 pi = sp[slot];
+        int nA = 0, nB = 0, nC = 0;
+        // pass 1: classify every candidate, count the classes
+        for (int base = 0; base < tot; base += 32) {
+            const int q = base + lane;
+            int cl = 0;
+            if (q < tot) {
+                const int j = sj[q];
+                if (j != i) {
+                    const int4 pj = sp[q];
+                    const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
+                    const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
+                    const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    bool in;
+                    if (r2 < D.rl2_lo_f) in = true;
+                    else if (r2 >= D.rl2_hi_f) in = false;
+                    else in = exact_r2(R, D.x[i], D.x[j]) < D.rl2;
+                    if (in) cl = r2 < R.rA2f ? 1 : (r2 < D.rc2_lo_f ? 2 : 3);
+                }
+                cls[q] = (unsigned char)cl;
+            }
+            nA += __popc(__ballot_sync(full, cl == 1));
+            nB += __popc(__ballot_sync(full, cl == 2));
+            nC += __popc(__ballot_sync(full, cl == 3));
+        }
+        __syncwarp();
+        // pass 2: write the row as A | B | C, each block in candidate order
+        int bA = 0, bB = nA, bC = nA + nB;
+        const unsigned below = (1u << lane) - 1u;
+        for (int base = 0; base < tot; base += 32) {
+            const int q = base + lane;
+            const int cl = q < tot ? cls[q] : 0;
+            const unsigned mA = __ballot_sync(full, cl == 1), mB = __ballot_sync(full, cl == 2),
+                           mC = __ballot_sync(full, cl == 3);
+            if (cl) {
+                const int pos = cl == 1 ? bA + __popc(mA & below) : (cl == 2 ? bB + __popc(mB & below)
+                                                                             : bC + __popc(mC & below));
+                if (pos < cap) D.nbr[(size_t)pos * stride + i] = sj[q];
+            }
+            bA += __popc(mA);
+            bB += __popc(mB);
+            bC += __popc(mC);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int n = nA + nB + nC;
+            D.nnb[i] = min(n, cap);
+            if (n > cap) set_err(D, HD_ERR_OVERFLOW, i, r);
+        }
     }
+    __syncthreads();  // the staging buffers are reused by the next cell
 }
 
-__global__ void __launch_bounds__(256, 4) k_nlist(Dev D) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+__device__ __forceinline__ void nl_smem_carve(const Dev &D, char *base, int4 *&sp, int *&sj, unsigned char *&scls) {
+    const int cmax = 27 * D.cell_cap;
+    sp = reinterpret_cast<int4 *>(base);
+    sj = reinterpret_cast<int *>(base + (size_t)cmax * sizeof(int4));
+    scls = reinterpret_cast<unsigned char *>(base + (size_t)cmax * (sizeof(int4) + sizeof(int)));
+}
+
+__global__ void __launch_bounds__(128) k_nlist(Dev D) {
+    extern __shared__ __align__(16) char nl_smem[];
+    __shared__ NlSmem M;
+    int4 *sp;
+    int *sj;
+    unsigned char *scls;
+    nl_smem_carve(D, nl_smem, sp, sj, scls);
     const int total = D.rb_off[D.nrep];
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int idx = blockIdx.x * (blockDim.x >> 5) + wib; idx < total; idx += nwarps) {
+    for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
         int lo = 0, hi = D.nrep - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (D.rb_off[mid] <= idx) lo = mid;
             else hi = mid - 1;
         }
-        dev_nlist_atom(D, lo, D.rep[lo].atom0 + (idx - D.rb_off[lo]), lane);
+        dev_nlist_cell(D, lo, idx - D.rb_off[lo], M, sp, sj, scls);
     }
 }
 
@@ -323,7 +373,7 @@ __global__ void __launch_bounds__(256, 4) k_nlist(Dev D) {
 // A = phi'/r, B = (phi'' - phi'/r)/r^2, with s = sigma_ab/r:
 //   -A = 24 eps s^6 (2 s^6 - 1)/r^2,   B = 96 eps s^6 (7 s^6 - 2)/r^4.
 // Q (quench): positions of the quench copy, no H.dr, quench partial sums.
-template <bool Q>
+template <bool Q, bool E>
 __device__ __forceinline__ void dev_pair64(const Dev &D, int t) {
     const int r = D.tile_rep[t];
     if (Q && D.st[r].q_done) return;
@@ -351,7 +401,7 @@ __device__ __forceinline__ void dev_pair64(const Dev &D, int t) {
             fx += fr * dx;
             fy += fr * dy;
             fz += fr * dz;
-            e += 0.5 * (4.0 * eps * s6 * (s6 - 1.0) - R.shift[ti][tj]);
+            if (E) e += 0.5 * (4.0 * eps * s6 * (s6 - 1.0) - R.shift[ti][tj]);
             if (!Q) {
                 const dbl4 drj = D.dr64[j];
                 const double ux = dri.x - drj.x, uy = dri.y - drj.y, uz = dri.z - drj.z;
@@ -360,6 +410,31 @@ __device__ __forceinline__ void dev_pair64(const Dev &D, int t) {
                 hx += -fr * ux + B * rdu * dx;
                 hy += -fr * uy + B * rdu * dy;
                 hz += -fr * uz + B * rdu * dz;
+            }
+        }
+    }
+    // harmonic bonds of Eq. 12, phi = k (r - r_b)^2 / 2 at any distance:
+    // A = phi'/r = k (r - r_b)/r, B = (phi'' - A)/r^2 = k r_b / r^3
+    if (R.nbond > 0 && act) {
+        for (int b = D.bond_off[i]; b < D.bond_off[i + 1]; ++b) {
+            const int j = D.bond_j[b];
+            const dbl4 xj = D.x[j];
+            const double dx = mi64(R, 0, xi.x - xj.x), dy = mi64(R, 1, xi.y - xj.y), dz = mi64(R, 2, xi.z - xj.z);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double rr = sqrt(r2), db = rr - R.rbond;
+            const double A = R.kbond * db / rr;
+            fx -= A * dx;
+            fy -= A * dy;
+            fz -= A * dz;
+            if (E) e += 0.5 * (0.5 * R.kbond * db * db);
+            if (!Q) {
+                const dbl4 drj = D.dr64[j];
+                const double ux = dri.x - drj.x, uy = dri.y - drj.y, uz = dri.z - drj.z;
+                const double rdu = dx * ux + dy * uy + dz * uz;
+                const double B = (R.kbond - A) / r2;
+                hx += A * ux + B * rdu * dx;
+                hy += A * uy + B * rdu * dy;
+                hz += A * uz + B * rdu * dz;
             }
         }
     }
@@ -416,7 +491,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-template <bool Q>
+template <bool Q, bool E>
 __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const int r = D.tile_rep[t];
     if (Q && D.st[r].q_done) return;
@@ -429,6 +504,8 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const float4 dri = Q ? make_float4(0.f, 0.f, 0.f, 0.f) : ai.d;
     const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
     const float e0 = R.epsf[ti][0], e1 = R.epsf[ti][1];
+    const float a0 = R.eps24f[ti][0], a1 = R.eps24f[ti][1];
+    const float b0 = R.eps96f[ti][0], b1 = R.eps96f[ti][1];
     const float h0 = R.shiftf[ti][0], h1 = R.shiftf[ti][1];
     const float q0h = R.r0sq_hi[ti][0], q1h = R.r0sq_hi[ti][1];
     const float q0l = R.r0sq_lo[ti][0], q1l = R.r0sq_lo[ti][1];
@@ -442,30 +519,39 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     // plain loads: in the persistent launch the list is rewritten between steps
     AtomRec an = D.rec[nn > 0 ? nb[0] : i];
     int jn = nn > 1 ? nb[stride] : i;
-    // one pair's contribution (cancellation-free LJ form, exact r^2 when the
-    // replica's axes share one fixed-point unit)
+    // one pair's contribution.  Cancellation-free LJ form: 2 s^6 - 1 = w(tt)
+    // with tt = (r_0^2 - r^2) / r^2.  Where |tt| < 1/4 (around the minimum,
+    // where w is small and the FP32 r^2 would cost it its relative accuracy)
+    // r^2 is taken exactly, as hi + lo, from the integer separations when the
+    // replica's axes share one fixed-point unit; elsewhere the FP32 r^2 gives
+    // w to a few ulps.  The list builder puts the pairs that can need the
+    // exact r^2 at the head of each row, so the branch is nearly uniform.
     auto term = [&](const AtomRec &aj, int ix, int iy, int iz, float dx, float dy, float dz, float r2) {
         const int tj = aj.p.w & 1;
-        const float eps = tj ? e1 : e0;
-        float r2h = r2, r2l = 0.f;
-        if (exact) r2_split(R, ix, iy, iz, r2h, r2l);
-        const float ir2 = rcp_approx(r2h);
-        const float tt = (((tj ? q1h : q0h) - r2h) + ((tj ? q1l : q0l) - r2l)) * ir2;
+        const float r0h = tj ? q1h : q0h, r0l = tj ? q1l : q0l;
+        float ir2 = rcp_approx(r2);
+        float tt = ((r0h - r2) + r0l) * ir2;
+        if (exact && fabsf(tt) < 0.25f) {
+            float r2h, r2l;
+            r2_split(R, ix, iy, iz, r2h, r2l);
+            ir2 = rcp_approx(r2h);
+            tt = ((r0h - r2h) + (r0l - r2l)) * ir2;
+        }
         const float u = 1.f + tt;
         const float s6 = 0.5f * u * u * u;
         const float w = tt * fmaf(tt, tt + 3.f, 3.f);          // 2 s^6 - 1
-        const float fr = 24.f * eps * ir2 * s6 * w;
+        const float fr = (tj ? a1 : a0) * ir2 * s6 * w;
         fx = fmaf(fr, dx, fx);
         fy = fmaf(fr, dy, fy);
         fz = fmaf(fr, dz, fz);
-        e = fmaf(0.5f, fmaf(4.f * eps * s6, s6 - 1.f, -(tj ? h1 : h0)), e);
+        if (E) e = fmaf(0.5f, fmaf(4.f * (tj ? e1 : e0) * s6, s6 - 1.f, -(tj ? h1 : h0)), e);
         if (!Q) {
             const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
             const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-            const float B = 96.f * eps * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
-            hx += fmaf(B, dx, -fr * ux);
-            hy += fmaf(B, dy, -fr * uy);
-            hz += fmaf(B, dz, -fr * uz);
+            const float B = (tj ? b1 : b0) * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
+            hx = fmaf(-fr, ux, fmaf(B, dx, hx));
+            hy = fmaf(-fr, uy, fmaf(B, dy, hy));
+            hz = fmaf(-fr, uz, fmaf(B, dz, hz));
         }
     };
     bool band = false;
@@ -496,6 +582,38 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (r2 >= D.rc2_lo_f && r2 < D.rc2_hi_f && exact_r2(R, xi64, D.x[j]) < D.rc2)
                 term(aj, ix, iy, iz, dx, dy, dz, r2);
+        }
+    }
+    // harmonic bonds of Eq. 12 at any distance, from the exact r^2 where the
+    // axes share one unit (r - r_b is a small difference of two numbers near
+    // r_b); A = k (r - r_b)/r, B = k r_b / r^3
+    if (R.nbond > 0 && act) {
+        for (int b = D.bond_off[i]; b < D.bond_off[i + 1]; ++b) {
+            const int j = D.bond_j[b];
+            const AtomRec aj = D.rec[j];
+            const int ix = (int)((unsigned)pi.x - (unsigned)aj.p.x);
+            const int iy = (int)((unsigned)pi.y - (unsigned)aj.p.y);
+            const int iz = (int)((unsigned)pi.z - (unsigned)aj.p.z);
+            const float dx = (float)ix * lx, dy = (float)iy * ly, dz = (float)iz * lz;
+            float r2h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), r2l = 0.f;
+            if (exact) r2_split(R, ix, iy, iz, r2h, r2l);
+            const float rh = sqrtf(r2h);
+            const float rr = rh + (fmaf(-rh, rh, r2h) + r2l) * (0.5f / rh);
+            const float db = (rr - R.rbond_hi) - R.rbond_lo;
+            const float ir = 1.f / rr;
+            const float A = R.kbondf * db * ir;
+            fx = fmaf(-A, dx, fx);
+            fy = fmaf(-A, dy, fy);
+            fz = fmaf(-A, dz, fz);
+            if (E) e = fmaf(0.25f * R.kbondf * db, db, e);
+            if (!Q) {
+                const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
+                const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+                const float B = (R.kbondf - A) * ir * ir * rdu;
+                hx = fmaf(A, ux, fmaf(B, dx, hx));
+                hy = fmaf(A, uy, fmaf(B, dy, hy));
+                hz = fmaf(A, uz, fmaf(B, dz, hz));
+            }
         }
     }
     // undo the FP32 rounding of the per-axis fixed-point unit (uniform per axis)
@@ -555,10 +673,10 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     }
 }
 
-template <bool Q>
-__global__ void __launch_bounds__(256) k_pair64(Dev D) { dev_pair64<Q>(D, blockIdx.x); }
-template <bool Q>
-__global__ void __launch_bounds__(256, 4) k_pair32(Dev D) { dev_pair32<Q>(D, blockIdx.x); }
+template <bool Q, bool E>
+__global__ void __launch_bounds__(256) k_pair64(Dev D) { dev_pair64<Q, E>(D, blockIdx.x); }
+template <bool Q, bool E>
+__global__ void __launch_bounds__(256, 4) k_pair32(Dev D) { dev_pair32<Q, E>(D, blockIdx.x); }
 
 // ---------------------------------------------------------------- per-replica scalars
 // Gathers the replica's tile sums (warp q sums slot q over the tiles in a
@@ -573,10 +691,11 @@ __global__ void __launch_bounds__(256, 4) k_pair32(Dev D) { dev_pair32<Q>(D, blo
 __device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, double ksum, RepState &S, Scal &C) {
     const RepDev &R = D.rep[r];
     const int nr = R.nrig, dim = R.dim, vert = R.vert;
+    const double xs = slider_x(R, S.step, D.dt);
     double xT[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
     if (nr > 0) {
         for (int a = 0; a < 3; ++a) xT[a] = acc[PART_XRIG + a] / (double)nr;
-        gs[0] = R.kspring * (xT[0] - R.slider[0]);
+        gs[0] = R.kspring * (xT[0] - xs);
         if (dim == 3) gs[1] = R.kspring * (xT[1] - R.slider[1]);
         gs[vert] = R.fnormal;
     }
@@ -597,14 +716,15 @@ __device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, do
         }
     double ext = 0.0;
     if (nr > 0) {
-        ext = 0.5 * R.kspring * (xT[0] - R.slider[0]) * (xT[0] - R.slider[0]);
+        ext = 0.5 * R.kspring * (xT[0] - xs) * (xT[0] - xs);
         if (dim == 3) ext += 0.5 * R.kspring * (xT[1] - R.slider[1]) * (xT[1] - R.slider[1]);
         ext += R.fnormal * xT[vert];
     }
     C.d = d; C.sigma = sig; C.dV = dV; C.dVp = dVp; C.G = G;
     C.Vlj = acc[PART_V];
     C.V = acc[PART_V] + ext;
-    C.FR = R.kspring * (R.slider[0] - xT[0]);
+    C.FR = R.kspring * (xs - xT[0]);
+    C.xS = xs;
     C.ca = ca; C.cb = cb;
     for (int a = 0; a < 3; ++a) { C.xT[a] = xT[a]; C.fbody[a] = fb[a]; }
     // clocks and the rigid body
@@ -675,6 +795,69 @@ __global__ void k_obs(Dev D) {
                                           S.vbody_full[2] * S.vbody_full[2]);
 }
 
+// ---------------------------------------------------------------- Nose-Hoover chain
+// One half step of the chain (Sec. 3.1.1; the reversible Trotter splitting of
+// Martyna, Tuckerman, Tobias and Klein, 1996, one stage): quarter kicks of
+// the chain velocities from the top down with exp(-v_{j+1} h/8) damping on
+// both sides, the particle scale s = exp(-v_1 h/2), the chain positions by
+// h/2, then the kicks from the bottom up.  k2 = sum m v^2 of the mobile atoms
+// is updated to its scaled value; returns s.
+__device__ double nhc_half(const RepDev &R, RepState &S, double &k2, double h) {
+    const int M = R.nhc_len;
+    const double kT = R.kT;
+    double *v = S.nhc_v;
+    auto force = [&](int j) {
+        return j == 0 ? (k2 - R.nhc_nf * kT) / R.nhc_Q[0] : (R.nhc_Q[j - 1] * v[j - 1] * v[j - 1] - kT) / R.nhc_Q[j];
+    };
+    v[M - 1] += 0.25 * h * force(M - 1);
+    for (int j = M - 2; j >= 0; --j) {
+        const double damp = exp(-0.125 * h * v[j + 1]);
+        v[j] *= damp;
+        v[j] += 0.25 * h * force(j);
+        v[j] *= damp;
+    }
+    const double sc = exp(-0.5 * h * v[0]);
+    k2 *= sc * sc;
+    for (int j = 0; j < M; ++j) S.nhc_xi[j] += 0.5 * h * v[j];
+    for (int j = 0; j < M - 1; ++j) {
+        const double damp = exp(-0.125 * h * v[j + 1]);
+        v[j] *= damp;
+        v[j] += 0.25 * h * force(j);
+        v[j] *= damp;
+    }
+    v[M - 1] += 0.25 * h * force(M - 1);
+    return sc;
+}
+
+// The chain between two kicks.  mode KIN: remember k2 of the current
+// velocities.  CLOSE: the closing half step of the step that ends (k2 from
+// the kinetic sums of the closing kick just made); OPEN: the opening half
+// step of the next one (k2 carried over).  C.nhc_scale is the product of the
+// particle scales, applied by the next update pass.
+__device__ void nhc_eval(const Dev &D, int r, int mode, double ksum, RepState &S, Scal &C) {
+    const RepDev &R = D.rep[r];
+    C.nhc_scale = 1.0;
+    if (R.nhc_len <= 0) return;
+    if (mode & MODE_KIN) {
+        S.nhc_k2 = 2.0 * ksum;
+        return;
+    }
+    double k2 = (mode & MODE_CLOSE) ? 2.0 * ksum : S.nhc_k2, sc = 1.0;
+    if (mode & MODE_CLOSE) sc *= nhc_half(R, S, k2, D.dt);
+    if (mode & MODE_OPEN) sc *= nhc_half(R, S, k2, D.dt);
+    S.nhc_k2 = k2;
+    C.nhc_scale = sc;
+}
+
+__global__ void k_nhc(Dev D, int mode) {
+    const int r = blockIdx.x;
+    const RepDev &R = D.rep[r];
+    double a = 0.0;
+    for (int t = R.tile0 + (int)threadIdx.x; t < R.tile0 + R.ntile; t += 32) a += D.kpart[t];
+    a = warp_sum(a);
+    if (threadIdx.x == 0) nhc_eval(D, r, mode, a, D.st[r], D.sc[r]);
+}
+
 // ---------------------------------------------------------------- integrator
 // BAOAB (reading: Langevin in place of the paper's Nose-Hoover chain):
 //   CLOSE: v += dt/2 F_tot                      (end of the previous step)
@@ -711,7 +894,14 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
             const double Fy = F.y + ca * (H.y - F.y) + cb * dr.y;
             const double Fz = F.z + ca * (H.z - F.z) + cb * dr.z;
             const bool three = R.dim == 3;
+            const bool chain = R.nhc_len > 0;
             if (mode & MODE_KIN) kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+            if ((mode & MODE_SCALE) && chain) {
+                v.x *= C.nhc_scale;
+                v.y *= C.nhc_scale;
+                v.z *= C.nhc_scale;
+                kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+            }
             if (mode & MODE_CLOSE) {
                 v.x += 0.5 * h * Fx;
                 v.y += 0.5 * h * Fy;
@@ -719,19 +909,26 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
                 kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
             if (mode & MODE_OPEN) {
+                if (chain && (mode & MODE_NHC)) {
+                    v.x *= C.nhc_scale;
+                    v.y *= C.nhc_scale;
+                    v.z *= C.nhc_scale;
+                }
                 v.x += 0.5 * h * Fx;
                 v.y += 0.5 * h * Fy;
                 if (three) v.z += 0.5 * h * Fz;
                 x.x += 0.5 * h * v.x;
                 x.y += 0.5 * h * v.y;
                 if (three) x.z += 0.5 * h * v.z;
-                double n0, n1, n2, n3;
-                normals64(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
-                v.x = R.c_ou * v.x + R.s_ou * n0;
-                v.y = R.c_ou * v.y + R.s_ou * n1;
-                if (three) {
-                    normals64(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
-                    v.z = R.c_ou * v.z + R.s_ou * n2;
+                if (!chain) {
+                    double n0, n1, n2, n3;
+                    normals64(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
+                    v.x = R.c_ou * v.x + R.s_ou * n0;
+                    v.y = R.c_ou * v.y + R.s_ou * n1;
+                    if (three) {
+                        normals64(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
+                        v.z = R.c_ou * v.z + R.s_ou * n2;
+                    }
                 }
                 x.x += 0.5 * h * v.x;
                 x.y += 0.5 * h * v.y;
@@ -757,7 +954,7 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
             post_move(D, R, r, i, x, p);
         }
     }
-    if (mode & (MODE_CLOSE | MODE_KIN)) {
+    if (mode & (MODE_CLOSE | MODE_KIN | MODE_SCALE)) {
         double v1[1] = {kin};
         cta_reduce<1>(v1, D.kpart + t, -1);
     }
@@ -784,7 +981,14 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
             const double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
             const double Fz = (double)fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
             const bool three = R.dim == 3;
+            const bool chain = R.nhc_len > 0;
             if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+            if ((mode & MODE_SCALE) && chain) {
+                v.x *= C.nhc_scale;
+                v.y *= C.nhc_scale;
+                v.z *= C.nhc_scale;
+                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+            }
             if (mode & MODE_CLOSE) {
                 v.x += hh * Fx;
                 v.y += hh * Fy;
@@ -792,17 +996,24 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
                 kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             }
             if (mode & MODE_OPEN) {
+                if (chain && (mode & MODE_NHC)) {
+                    v.x *= C.nhc_scale;
+                    v.y *= C.nhc_scale;
+                    v.z *= C.nhc_scale;
+                }
                 v.x += hh * Fx;
                 v.y += hh * Fy;
                 if (three) v.z += hh * Fz;
                 const double ax = v.x, ay = v.y, az = v.z;
-                float n0, n1, n2, n3;
-                normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
-                v.x = R.c_ou * v.x + R.s_ou * (double)n0;
-                v.y = R.c_ou * v.y + R.s_ou * (double)n1;
-                if (three) {
-                    normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
-                    v.z = R.c_ou * v.z + R.s_ou * (double)n2;
+                if (!chain) {
+                    float n0, n1, n2, n3;
+                    normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
+                    v.x = R.c_ou * v.x + R.s_ou * (double)n0;
+                    v.y = R.c_ou * v.y + R.s_ou * (double)n1;
+                    if (three) {
+                        normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
+                        v.z = R.c_ou * v.z + R.s_ou * (double)n2;
+                    }
                 }
                 x.x += hh * (ax + v.x);
                 x.y += hh * (ay + v.y);
@@ -828,7 +1039,7 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
             post_move(D, R, r, i, x, p);
         }
     }
-    if (mode & (MODE_CLOSE | MODE_KIN)) {
+    if (mode & (MODE_CLOSE | MODE_KIN | MODE_SCALE)) {
         double v1[1] = {(double)warp_sum(kin)};
         if ((threadIdx.x & 31) != 0) v1[0] = 0.0;
         cta_reduce<1>(v1, D.kpart + t, -1);
@@ -897,7 +1108,7 @@ __global__ void k_qscalar(Dev D, int max_iter) {
     if (nr > 0) {
         double xT[3], gs[3] = {0, 0, 0};
         for (int a = 0; a < 3; ++a) xT[a] = acc[QP_XRIG + a] / (double)nr;
-        gs[0] = R.kspring * (xT[0] - R.slider[0]);
+        gs[0] = R.kspring * (xT[0] - slider_x(R, S.step, D.dt));   // the slider stands still during a quench
         if (dim == 3) gs[1] = R.kspring * (xT[1] - R.slider[1]);
         gs[R.vert] = R.fnormal;
         for (int a = 0; a < 3; ++a) fb[a] = acc[QP_FRIG + a] - gs[a];
@@ -1105,6 +1316,12 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
     __shared__ Scal C;
     __shared__ double acc[NPART + 1];
     __shared__ int s_flag;
+    __shared__ NlSmem M;
+    extern __shared__ __align__(16) char nl_smem[];
+    int4 *sp;
+    int *sj;
+    unsigned char *scls;
+    nl_smem_carve(D, nl_smem, sp, sj, scls);
     if (threadIdx.x == 0) {
         S = D.st[r];
         C = D.sc[r];
@@ -1128,9 +1345,24 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
             else dev_update32(D, t, mode, C);
         }
     };
+    // the chain between the kicks (every CTA evaluates it alike from the
+    // replica's kinetic sums)
+    auto chain = [&](int mode) {
+        dev_scalar_acc(D, r, acc);
+        if (threadIdx.x == 0) {
+            nhc_eval(D, r, mode, acc[NPART], S, C);
+            if (leader) {
+                D.st[r] = S;
+                D.sc[r] = C;
+            }
+        }
+        __syncthreads();
+    };
+    const bool nhc = D.any_nhc != 0;
     // opening half of the first step, from the forces of the last call
     scalars(MODE_OPEN);
-    update(MODE_OPEN);
+    if (nhc) chain(MODE_OPEN);
+    update(nhc ? (MODE_OPEN | MODE_NHC) : MODE_OPEN);
     if (!grp_barrier(D, r, nc, epoch)) return;
     for (int k = 1; k <= nsteps; ++k) {
         if (threadIdx.x == 0) s_flag = *((volatile int *)(D.rebuild + r));
@@ -1148,19 +1380,31 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
                 if (flag == 1) S.n_rebuild += 1;
                 if (leader) D.rebuild[r] = 0;
             }
-            const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc)
-                for (int a = wib; a < D.tile_n[t]; a += nw) dev_nlist_atom(D, r, D.tile_start[t] + a, lane);
-            __syncthreads();
+            // rows are built cell by cell, so a CTA's tiles take rows other CTAs wrote
+            for (int c = me; c < R.ncell; c += nc) dev_nlist_cell(D, r, c, M, sp, sj, scls);
+            if (!grp_barrier(D, r, nc, epoch)) return;
         }
         for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc) {
-            if (PREC == HD_FP64) dev_pair64<false>(D, t);
-            else dev_pair32<false>(D, t);
+            // per-atom energies (observables only) on the last step of the call
+            if (PREC == HD_FP64) {
+                if (k == nsteps) dev_pair64<false, true>(D, t);
+                else dev_pair64<false, false>(D, t);
+            } else {
+                if (k == nsteps) dev_pair32<false, true>(D, t);
+                else dev_pair32<false, false>(D, t);
+            }
         }
         if (!grp_barrier(D, r, nc, epoch)) return;
         const int mode = k < nsteps ? (MODE_CLOSE | MODE_OPEN) : MODE_CLOSE;
         scalars(mode);
-        update(mode);
+        if (!nhc) {
+            update(mode);
+        } else {
+            update(MODE_CLOSE);
+            if (!grp_barrier(D, r, nc, epoch)) return;
+            chain(mode);
+            update((mode & MODE_OPEN) ? (MODE_OPEN | MODE_NHC) : MODE_SCALE);
+        }
         if (!grp_barrier(D, r, nc, epoch)) return;
     }
     if (leader && threadIdx.x == 0) D.st[r] = S;
@@ -1168,6 +1412,22 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
 
 // ---------------------------------------------------------------- launchers
 static inline int nthr(const Dev &D) { return D.block; }
+
+// Dynamic shared memory of the list build: positions, indices and classes
+// of up to 27 cells of cell_cap candidates (classes: one byte per candidate
+// for each of the warps of a 128-thread CTA).
+size_t nl_smem_bytes(const Dev &D) {
+    const size_t cmax = 27 * (size_t)D.cell_cap;
+    return cmax * (sizeof(int4) + sizeof(int)) + cmax * 4;
+}
+cudaError_t nl_configure(const Dev &D) {
+    const int bytes = (int)nl_smem_bytes(D);
+    cudaError_t e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_persist<HD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_persist<HD_FP32_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s) {
     k_init<<<D.ntile, nthr(D), 0, s>>>(D, draw_vel);
@@ -1177,15 +1437,17 @@ void launch_rebuild(const Dev &D, cudaStream_t s) {
     k_bin<<<D.ntile, nthr(D), 0, s>>>(D);
     k_cellsort<<<dim3((D.max_cells + 127) / 128, D.nrep), 128, 0, s>>>(D);
     k_rebuild_plan<<<1, 32, 0, s>>>(D);
-    k_nlist<<<D.nl_grid, 256, 0, s>>>(D);
+    k_nlist<<<D.nl_grid, 128, nl_smem_bytes(D), s>>>(D);
 }
-void launch_pair(const Dev &D, bool quench, cudaStream_t s) {
+void launch_pair(const Dev &D, bool quench, bool energy, cudaStream_t s) {
     if (D.prec == HD_FP64) {
-        if (quench) k_pair64<true><<<D.ntile, nthr(D), 0, s>>>(D);
-        else k_pair64<false><<<D.ntile, nthr(D), 0, s>>>(D);
+        if (quench) k_pair64<true, false><<<D.ntile, nthr(D), 0, s>>>(D);
+        else if (energy) k_pair64<false, true><<<D.ntile, nthr(D), 0, s>>>(D);
+        else k_pair64<false, false><<<D.ntile, nthr(D), 0, s>>>(D);
     } else {
-        if (quench) k_pair32<true><<<D.ntile, nthr(D), 0, s>>>(D);
-        else k_pair32<false><<<D.ntile, nthr(D), 0, s>>>(D);
+        if (quench) k_pair32<true, false><<<D.ntile, nthr(D), 0, s>>>(D);
+        else if (energy) k_pair32<false, true><<<D.ntile, nthr(D), 0, s>>>(D);
+        else k_pair32<false, false><<<D.ntile, nthr(D), 0, s>>>(D);
     }
 }
 void launch_scalar(const Dev &D, int mode, cudaStream_t s) {
@@ -1196,18 +1458,20 @@ void launch_update(const Dev &D, int mode, cudaStream_t s) {
     else k_update32<<<D.ntile, nthr(D), 0, s>>>(D, mode);
 }
 void launch_obs(const Dev &D, cudaStream_t s) { k_obs<<<D.nrep, 32, 0, s>>>(D); }
+void launch_nhc(const Dev &D, int mode, cudaStream_t s) { k_nhc<<<D.nrep, 32, 0, s>>>(D, mode); }
 void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s) { k_qinit<<<Q.ntile, nthr(Q), 0, s>>>(Q, M); }
 void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s) {
     launch_rebuild(Q, s);
-    launch_pair(Q, true, s);
+    launch_pair(Q, true, false, s);
     k_qscalar<<<Q.nrep, 32 * QPART, 0, s>>>(Q, max_iter);
     k_qupdate<<<Q.ntile, nthr(Q), 0, s>>>(Q);
 }
 void launch_qdisp(const Dev &Q, cudaStream_t s) { k_qdisp<<<Q.ntile, nthr(Q), 0, s>>>(Q); }
-int persist_blocks_per_sm(int prec, int block) {
+int persist_blocks_per_sm(const Dev &D) {
     int nb = 0;
-    if (prec == HD_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP64>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP32_SPLIT>, block, 0);
+    const size_t sm = nl_smem_bytes(D);
+    if (D.prec == HD_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP64>, D.block, sm);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP32_SPLIT>, D.block, sm);
     return nb;
 }
 cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s) {
@@ -1218,7 +1482,7 @@ cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(D.block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = nl_smem_bytes(D);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

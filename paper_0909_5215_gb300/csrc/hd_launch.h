@@ -1,5 +1,5 @@
-// hd_launch.h -- host-side launchers of the kernels in hd_kernels.cu and
-// hd_persist.cu.  Every launcher queues work on stream s and returns at once.
+// hd_launch.h -- host-side launchers of the kernels in hd_kernels.cu.  Every
+// launcher queues work on stream s and returns at once.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -8,16 +8,20 @@
 namespace hd {
 
 void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s);
-void launch_rebuild(const Dev &D, cudaStream_t s);            // 3 kernels, flag-gated per replica
-void launch_pair(const Dev &D, bool quench, cudaStream_t s);
+void launch_rebuild(const Dev &D, cudaStream_t s);            // 5 kernels, flag-gated per replica
+// energy: also compute per-atom LJ energies (observables only; not needed by the dynamics)
+void launch_pair(const Dev &D, bool quench, bool energy, cudaStream_t s);
 void launch_scalar(const Dev &D, int mode, cudaStream_t s);
 void launch_update(const Dev &D, int mode, cudaStream_t s);
 void launch_obs(const Dev &D, cudaStream_t s);
+void launch_nhc(const Dev &D, int mode, cudaStream_t s);          // the chain between two kicks, per replica
 void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s);
 void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 6 kernels
 void launch_qdisp(const Dev &Q, cudaStream_t s);
 void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s);
-int persist_blocks_per_sm(int prec, int block);                   // resident CTAs of the persistent kernel
+size_t nl_smem_bytes(const Dev &D);                               // dynamic shared memory of the list build
+cudaError_t nl_configure(const Dev &D);                           // allow that much on the kernels that build lists
+int persist_blocks_per_sm(const Dev &D);                          // resident CTAs of the persistent kernel
 cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s);  // cooperative, n steps
 
 }  // namespace hd

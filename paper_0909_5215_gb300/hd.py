@@ -24,8 +24,9 @@ HD_DRIVER_AUTO, HD_DRIVER_KERNELS, HD_DRIVER_PERSISTENT = 0, 1, 2
  F_ENERGY) = range(11)
 OBS_FIELDS = ["step", "t_md", "t_h", "V", "K", "dV", "sigma", "d", "F_R", "x_T", "y_T", "z_T",
               "n_rebuild", "boost", "q_iter", "q_fmax", "G", "fbody_x", "fbody_y", "fbody_z",
-              "vbody_x", "vbody_y", "vbody_z", "q_disp", "n_dv_zero", "n_dv_band", "n_dv_max", "q_conv"]
-OBS_LEN = 28
+              "vbody_x", "vbody_y", "vbody_z", "q_disp", "n_dv_zero", "n_dv_band", "n_dv_max", "q_conv",
+              "x_S", "nhc_energy", "reserved30", "reserved31"]
+OBS_LEN = 32
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_NOMEM", 4: "HD_ERR_NUMERIC",
                 5: "HD_ERR_TIMEOUT", 6: "HD_ERR_STATE", 7: "HD_ERR_UNIMPLEMENTED", 8: "HD_ERR_OVERFLOW"}
 
@@ -47,6 +48,10 @@ class hd_replica_desc(C.Structure):
         ("dvmax", C.c_double), ("sig_lo", C.c_double), ("sig_hi", C.c_double),
         ("eps", (C.c_double * 2) * 2), ("sig", (C.c_double * 2) * 2),
         ("t_h0", C.c_double), ("t_md0", C.c_double), ("step0", C.c_int64),
+        ("v_slide", C.c_double),
+        ("n_bonds", C.c_int), ("pad2_", C.c_int), ("bonds", C.POINTER(C.c_int32)),
+        ("k_bond", C.c_double), ("r_bond", C.c_double),
+        ("nhc_len", C.c_int), ("pad3_", C.c_int), ("nhc_tau", C.c_double),
     ]
 
 
@@ -177,17 +182,10 @@ def make_params(params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, pre
 def make_descs(reps):
     """Build the C descriptors; returns (array, keep-alive list).  Replicas
     asking for what the library does not compute (the eigenvalue bias of
-    Eq. 13/15, continuous sliding, harmonic tip bonds of Eq. 12, the
-    Nose-Hoover chain) are refused rather than run without it."""
+    Eq. 13/15) are refused rather than run without it."""
     for k, r in enumerate(reps):
-        if getattr(r, "nhc_len", 0):
-            raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: the Nose-Hoover chain is not implemented on the GPU" % k)
         if getattr(r, "eig_on", 0):
             raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: the eigenvalue bias is not implemented on the GPU" % k)
-        if getattr(r, "v_slide", 0.0):
-            raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: continuous sliding is not implemented on the GPU" % k)
-        if getattr(r, "bonds", None) is not None and len(r.bonds):
-            raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: harmonic tip bonds are not implemented on the GPU" % k)
     keep = []
     arr = (hd_replica_desc * len(reps))()
 
@@ -219,6 +217,16 @@ def make_descs(reps):
                 d.eps[a][b] = float(r.eps[a][b])
                 d.sig[a][b] = float(r.sig[a][b])
         d.t_h0, d.t_md0, d.step0 = float(r.t_h0), float(r.t_md0), int(r.step0)
+        d.v_slide = float(getattr(r, "v_slide", 0.0))
+        bonds = getattr(r, "bonds", None)
+        if bonds is not None and len(bonds):
+            bnd = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+            keep.append(bnd)
+            d.n_bonds = len(bnd)
+            d.bonds = bnd.ctypes.data_as(C.POINTER(C.c_int32))
+            d.k_bond, d.r_bond = float(r.k_bond), float(r.r_bond)
+        d.nhc_len = int(getattr(r, "nhc_len", 0))
+        d.nhc_tau = float(getattr(r, "nhc_tau", 0.5))
     return arr, keep
 
 

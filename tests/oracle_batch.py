@@ -8,7 +8,7 @@ set_bias follows hd_set_bias (rows of DeltaV_max, sigma_L, sigma_U, m).
 """
 import numpy as np
 
-OBS_LEN = 28
+OBS_LEN = 32
 
 
 class OracleBatch:

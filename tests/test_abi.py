@@ -174,29 +174,43 @@ def test_eigenvalue_bias_is_refused_not_dropped():
     hd.make_descs([small2d()])
 
 
-def test_continuous_sliding_is_refused_not_dropped():
+def test_continuous_sliding_reaches_the_descriptor():
+    """A moving slider (Sec. 3.1.1, method 1) is carried into the C descriptor."""
     from conftest import small2d
     from paper_0909_5215_gb300 import hd
     r = small2d()
     r.v_slide = 1e-3
-    with pytest.raises(hd.HdError) as ei:
-        hd.make_descs([r])
-    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
+    descs, _keep = hd.make_descs([r, small2d()])
+    assert descs[0].v_slide == 1e-3 and descs[1].v_slide == 0.0
 
 
-def test_tip_bonds_are_refused_not_dropped():
+def test_tip_bonds_reach_the_descriptor():
+    """The paper's bonded 3-D tip (Eq. 12) is carried into the C descriptor."""
     from paper_0909_5215_gb300 import hd
     from paper_0909_5215_gb300 import model as M
-    with pytest.raises(hd.HdError) as ei:
-        hd.make_descs([M.paper3d()])
-    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
+    r = M.paper3d()
+    descs, _keep = hd.make_descs([r])
+    assert descs[0].n_bonds == len(r.bonds) > 0
+    assert descs[0].k_bond == 57.2 and descs[0].r_bond == 1.12
+    assert [descs[0].bonds[k] for k in range(4)] == [int(v) for v in r.bonds[:2].reshape(-1)]
 
 
-def test_nose_hoover_chain_is_refused_not_dropped():
+def test_bad_bond_index_is_refused(hdlib):
+    from paper_0909_5215_gb300 import model as M
+    r = M.paper2d()
+    r.bonds = np.array([[0, r.n]], dtype=np.int32)
+    p = M.Params(prec=1)
+    descs, keep = hdlib.make_descs([r])
+    assert hdlib.hd_workspace_bytes(descs, 1, hdlib.make_params(p)) == 0
+
+
+def test_nose_hoover_chain_reaches_the_descriptor(hdlib):
     from conftest import small2d
-    from paper_0909_5215_gb300 import hd
     r = small2d()
-    r.nhc_len = 3
-    with pytest.raises(hd.HdError) as ei:
-        hd.make_descs([r])
-    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
+    r.nhc_len, r.nhc_tau = 3, 0.7
+    descs, _keep = hdlib.make_descs([r])
+    assert descs[0].nhc_len == 3 and descs[0].nhc_tau == 0.7
+    r.nhc_len = 9                        # longer than the library's chain
+    descs, _keep = hdlib.make_descs([r])
+    from paper_0909_5215_gb300 import model as M
+    assert hdlib.hd_workspace_bytes(descs, 1, hdlib.make_params(M.Params())) == 0

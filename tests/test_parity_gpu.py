@@ -358,12 +358,12 @@ def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_stat
 @pytest.mark.parametrize("prec", [0, 1])
 def test_quench_fire_3d_workload_model(hd, oracle_mod, workload_states, prec):
     """FIRE on the 14,272-atom 3-D model from a thermal state, to 1e-6 (FP64)
-    or 1e-4 (split): both converge, find the same minimum, and agree on the
-    transition test."""
+    or 1e-3 (split: the floor of the rigid body's summed FP32 force): both
+    converge, find the same minimum, and agree on the transition test."""
     st = workload_states[1]
     p = _params(prec=prec, bias_on=1)
     b = hd.Batch([st], p)
-    ftol = 1e-6 if prec == 0 else 1e-4
+    ftol = 1e-6 if prec == 0 else 1e-3
     flags = b.quench(method=1, ftol=ftol, max_iter=20000, step_size=0.005, theta=0.5, adopt=0)
     o = oracle_mod.OracleReplica(st, p)
     xq, it, fm = o.quench(method=1, ftol=ftol, max_iter=20000, step_size=0.005)
@@ -379,16 +379,20 @@ def test_quench_fire_3d_workload_model(hd, oracle_mod, workload_states, prec):
 def test_quench_sd_3d_workload_model(hd, oracle_mod, workload_states, prec):
     """Steepest descent on the 14,272-atom 3-D model: 300 iterations of the same
     step give the same positions (the iteration is contractive, so the FP32
-    forces of the split form stay within their own error)."""
+    forces of the split form stay within their own error).  The library
+    reports the largest force at the final positions; the oracle returns the
+    one it tested before its last move, so that is taken from a 301-iteration
+    run."""
     st = workload_states[1]
     p = _params(prec=prec, bias_on=1)
     b = hd.Batch([st], p)
     b.quench(method=0, ftol=1e-12, max_iter=300, step_size=0.002, theta=0.5, adopt=0)
     o = oracle_mod.OracleReplica(st, p)
     xq, it, fm = o.quench(method=0, ftol=1e-12, max_iter=300, step_size=0.002)
+    _, it1, fm1 = o.quench(method=0, ftol=1e-12, max_iter=301, step_size=0.002)
     ob = b.obs(0)
-    assert ob["q_iter"] == it == 300 and ob["q_conv"] == 0.0
-    assert ob["q_fmax"] == pytest.approx(fm, rel=1e-9 if prec == 0 else 1e-3)
+    assert ob["q_iter"] == it == 300 and it1 == 301 and ob["q_conv"] == 0.0
+    assert ob["q_fmax"] == pytest.approx(fm1, rel=1e-9 if prec == 0 else 1e-3)
     assert np.abs(b.qpos(0) - xq).max() < (1e-9 if prec == 0 else 1e-5)
     # an unconverged quench never becomes r_O
     b.quench(method=0, ftol=1e-12, max_iter=50, step_size=0.002, theta=0.0, adopt=2)
