@@ -40,19 +40,23 @@ __device__ __forceinline__ void cta_reduce(double (&v)[NV], double *out, int max
     __syncthreads();
 }
 
-// Tile sums of the split form: slots [0, nf) are FP32 per-atom values summed
-// in FP32 within each warp; xr (rigid positions, FP64) go to slots
+// Tile sums of the split form: slots PART_D2, PART_G, PART_V are per-atom
+// FP64 values (products of FP32 factors, exact in FP64) summed in FP64, since
+// sigma = G / d (Eq. 5) feeds the bias; slots [3, nf) are FP32 per-atom values
+// summed in FP32 within each warp; xr (rigid positions, FP64) go to slots
 // PART_XRIG..+2 when some lane holds a rigid atom.  Warp results are added in
 // FP64 in warp order.  Slots never written by a warp count as zero.
-__device__ __forceinline__ void tile_reduce_mixed(float (&v)[12], int nf, double (&xr)[3], bool anyrig,
-                                                  double *out) {
+__device__ __forceinline__ void tile_reduce_mixed(double (&d3)[3], float (&v)[12], int nf, double (&xr)[3],
+                                                  bool anyrig, double *out) {
     __shared__ double sm[32][NPART];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     double wsum[NPART];
 #pragma unroll
     for (int q = 0; q < NPART; ++q) wsum[q] = 0.0;
 #pragma unroll
-    for (int q = 0; q < 12; ++q)
+    for (int q = 0; q < 3; ++q) wsum[q] = warp_sum(d3[q]);
+#pragma unroll
+    for (int q = 3; q < 12; ++q)
         if (q < nf) wsum[q] = (double)warp_sum(v[q]);
     if (anyrig)
 #pragma unroll
@@ -70,8 +74,12 @@ __device__ __forceinline__ void tile_reduce_mixed(float (&v)[12], int nf, double
     __syncthreads();
 }
 
-// Quench tile sums: slot QP_FMAX2 is a max, the others sums (FP32 in warps).
-__device__ __forceinline__ void tile_reduce_quench(float (&v)[12], double (&xr)[3], bool anyrig, double *out) {
+// Quench tile sums: slot QP_FMAX2 is a max; FIRE's power F.v, v.v and F.F
+// (pvf, FP64 per-atom products of FP32 factors) are summed in FP64, since the
+// sign of the power near convergence is a small difference of large sums; the
+// rigid forces are FP32 sums within warps.
+__device__ __forceinline__ void tile_reduce_quench(float (&v)[12], double (&pvf)[3], double (&xr)[3], bool anyrig,
+                                                   double *out) {
     __shared__ double sm[32][NPART];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     double wsum[NPART];
@@ -81,9 +89,9 @@ __device__ __forceinline__ void tile_reduce_quench(float (&v)[12], double (&xr)[
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
     wsum[QP_FMAX2] = (double)m;
-    wsum[QP_P] = (double)warp_sum(v[QP_P]);
-    wsum[QP_VV] = (double)warp_sum(v[QP_VV]);
-    wsum[QP_FF] = (double)warp_sum(v[QP_FF]);
+    wsum[QP_P] = warp_sum(pvf[0]);
+    wsum[QP_VV] = warp_sum(pvf[1]);
+    wsum[QP_FF] = warp_sum(pvf[2]);
     if (anyrig) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -164,28 +172,32 @@ __device__ __forceinline__ void dev_bin(const Dev &D, int t) {
 }
 __global__ void k_bin(Dev D) { dev_bin(D, blockIdx.x); }
 
-// Each cell's atom list in ascending slot order (one thread per cell).  With
-// atoms stored cell-major, walking the neighbour cells in ascending cell
-// order then yields candidates in (almost) ascending j.
-__device__ __forceinline__ void dev_cellsort_one(const Dev &D, const RepDev &R, int c) {
+// Each cell's atom list in ascending slot order: one warp per cell copies the
+// list to shared memory and writes every entry at its rank (slot indices are
+// distinct).  With atoms stored cell-major, walking the neighbour cells in
+// ascending cell order then yields candidates in (almost) ascending j.
+__device__ __forceinline__ void dev_cellsort_warp(const Dev &D, const RepDev &R, int c, int *buf) {
+    const int lane = threadIdx.x & 31;
     int *a = D.cell_atoms + (size_t)(R.cell0 + c) * D.cell_cap;
     const int m = min(D.cell_cnt[R.cell0 + c], D.cell_cap);
-    for (int k = 1; k < m; ++k) {
-        const int v = a[k];
-        int q = k;
-        while (q > 0 && a[q - 1] > v) {
-            a[q] = a[q - 1];
-            --q;
-        }
-        a[q] = v;
+    for (int k = lane; k < m; k += 32) buf[k] = a[k];
+    __syncwarp();
+    for (int k = lane; k < m; k += 32) {
+        const int v = buf[k];
+        int rank = 0;
+        for (int q = 0; q < m; ++q) rank += buf[q] < v;
+        a[rank] = v;
     }
+    __syncwarp();
 }
-__global__ void k_cellsort(Dev D) {
+__global__ void __launch_bounds__(128) k_cellsort(Dev D) {
+    extern __shared__ int cs_buf[];
     const int r = blockIdx.y;
     if (!D.rebuild[r]) return;
     const RepDev &R = D.rep[r];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < R.ncell) dev_cellsort_one(D, R, c);
+    const int w = threadIdx.x >> 5;
+    const int c = blockIdx.x * (blockDim.x >> 5) + w;
+    if (c < R.ncell) dev_cellsort_warp(D, R, c, cs_buf + w * D.cell_cap);
 }
 
 // Prefix of the cell counts of the replicas whose rebuild flag is set:
@@ -229,53 +241,92 @@ __device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSme
     const int m = min(D.cell_cnt[cell0], D.cell_cap);
     if (m == 0) return;  // uniform: every thread reads the same count
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) {
+    if (w == 0) {
+        // lane k < 27: stencil cell (k % 3, k / 3 % 3, k / 9) of the per-axis
+        // lists, each list ascending (a periodic wrap puts nc-1 after 0 and 1)
         const int ci[3] = {c % R.nc[0], (c / R.nc[0]) % R.nc[1], c / (R.nc[0] * R.nc[1])};
-        int cs[3][3], ncs[3];
+        int cs[3], ncs[3];
+        const int pick[3] = {lane % 3, (lane / 3) % 3, lane / 9};
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int nc = R.nc[a];
-            ncs[a] = 0;
+            const int nc = R.nc[a], q = pick[a];
+            int list[3] = {0, 0, 0}, n = 0;
             if (nc == 1) {
-                cs[a][ncs[a]++] = 0;
+                list[n++] = 0;
             } else {
-                // ascending: a periodic wrap puts nc-1 after 0 and 1
                 const int c0 = ci[a] - 1, c2 = ci[a] + 1;
                 if (R.periodic[a]) {
-                    if (c0 < 0) { cs[a][0] = 0; cs[a][1] = 1; cs[a][2] = nc - 1; }
-                    else if (c2 >= nc) { cs[a][0] = 0; cs[a][1] = nc - 2; cs[a][2] = nc - 1; }
-                    else { cs[a][0] = c0; cs[a][1] = ci[a]; cs[a][2] = c2; }
-                    ncs[a] = 3;
+                    if (c0 < 0) { list[0] = 0; list[1] = 1; list[2] = nc - 1; }
+                    else if (c2 >= nc) { list[0] = 0; list[1] = nc - 2; list[2] = nc - 1; }
+                    else { list[0] = c0; list[1] = ci[a]; list[2] = c2; }
+                    n = 3;
                 } else {
-                    if (c0 >= 0) cs[a][ncs[a]++] = c0;
-                    cs[a][ncs[a]++] = ci[a];
-                    if (c2 < nc) cs[a][ncs[a]++] = c2;
+                    if (c0 >= 0) list[n++] = c0;
+                    list[n++] = ci[a];
+                    if (c2 < nc) list[n++] = c2;
                 }
             }
+            ncs[a] = n;
+            cs[a] = q < n ? list[q] : 0;
         }
-        int k = 0, tot = 0;
-        for (int iz = 0; iz < ncs[2]; ++iz)
-            for (int iy = 0; iy < ncs[1]; ++iy)
-                for (int ix = 0; ix < ncs[0]; ++ix) {
-                    const int cc = R.cell0 + (cs[2][iz] * R.nc[1] + cs[1][iy]) * R.nc[0] + cs[0][ix];
-                    if (cc == cell0) M.kc = k;
-                    M.cell[k] = cc;
-                    M.off[k] = tot;
-                    tot += min(D.cell_cnt[cc], D.cell_cap);
-                    ++k;
-                }
-        M.off[k] = tot;
-        M.nst = k;
-        M.tot = tot;
+        const bool valid = lane < 27 && pick[0] < ncs[0] && pick[1] < ncs[1] && pick[2] < ncs[2];
+        const int nst = ncs[0] * ncs[1] * ncs[2];
+        const int k = valid ? (pick[2] * ncs[1] + pick[1]) * ncs[0] + pick[0] : 0;
+        const int cc = R.cell0 + (cs[2] * R.nc[1] + cs[1]) * R.nc[0] + cs[0];
+        if (valid) {
+            M.cell[k] = cc;
+            M.off[k] = min(D.cell_cnt[cc], D.cell_cap);   // the count, until the scan below
+            if (cc == cell0) M.kc = k;
+        }
+        __syncwarp();
+        // exclusive scan of the counts in stencil order
+        const int cnt = lane < nst ? M.off[lane] : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        __syncwarp();
+        if (lane < nst) M.off[lane] = incl - cnt;
+        if (lane == nst - 1) {
+            M.off[nst] = incl;
+            M.tot = incl;
+            M.nst = nst;
+        }
     }
     __syncthreads();
-    // stage the stencil: warp q copies stencil cells q, q + nw, ...
-    for (int k = w; k < M.nst; k += nw) {
-        const int *ca = D.cell_atoms + (size_t)M.cell[k] * D.cell_cap;
-        const int o = M.off[k], n = M.off[k + 1] - o;
-        for (int t = lane; t < n; t += 32) {
-            const int j = ca[t];
-            sj[o + t] = j;
-            sp[o + t] = D.rec[j].p;
+    // stage the stencil: every thread takes candidates idx, idx + blockDim, ...,
+    // four at a time so that their loads are in flight together
+    {
+        const int tot = M.tot, nst = M.nst;
+        for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
+            int jj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * blockDim.x;
+                jj[u] = -1;
+                if (idx < tot) {
+                    int lo = 0, hi = nst - 1;          // last stencil cell with off <= idx
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (M.off[mid] <= idx) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    jj[u] = D.cell_atoms[(size_t)M.cell[lo] * D.cell_cap + (idx - M.off[lo])];
+                }
+            }
+            int4 pp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) pp[u] = jj[u] >= 0 ? D.rec[jj[u]].p : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * blockDim.x;
+                if (idx < tot) {
+                    sj[idx] = jj[u];
+                    sp[idx] = pp[u];
+                }
+            }
         }
     }
     __syncthreads();
@@ -634,10 +685,12 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     // FP32 sums inside each warp, FP64 across warps and tiles
     if (!Q) {
         float v[12] = {};
+        double d3[3] = {0.0, 0.0, 0.0};
         if (act) {
-            v[PART_D2] = dri.x * dri.x + dri.y * dri.y + dri.z * dri.z;
-            v[PART_G] = -(fx * dri.x + fy * dri.y + fz * dri.z);
-            v[PART_V] = e;
+            const double rx = dri.x, ry = dri.y, rz = dri.z;
+            d3[PART_D2] = rx * rx + ry * ry + rz * rz;
+            d3[PART_G] = -((double)fx * rx + (double)fy * ry + (double)fz * rz);
+            d3[PART_V] = (double)e;
         }
         if (rig) {
             v[PART_FRIG] = fx; v[PART_FRIG + 1] = fy; v[PART_FRIG + 2] = fz;
@@ -649,16 +702,18 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
             const dbl4 xi = D.x[i];
             xr[0] = xi.x; xr[1] = xi.y; xr[2] = xi.z;
         }
-        tile_reduce_mixed(v, anyrig ? 12 : 3, xr, anyrig, D.part + (size_t)t * NPART);
+        tile_reduce_mixed(d3, v, anyrig ? 12 : 3, xr, anyrig, D.part + (size_t)t * NPART);
     } else {
         float v[12] = {};
+        double pvf[3] = {0.0, 0.0, 0.0};
         float fm = 0.f;
         if (role == ROLE_MOBILE) {
             const float4 vv = D.v32[i];
             fm = fx * fx + fy * fy + fz * fz;
-            v[QP_P] = fx * vv.x + fy * vv.y + fz * vv.z;
-            v[QP_VV] = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
-            v[QP_FF] = fm;
+            const double gx = fx, gy = fy, gz = fz, ux = vv.x, uy = vv.y, uz = vv.z;
+            pvf[0] = gx * ux + gy * uy + gz * uz;
+            pvf[1] = ux * ux + uy * uy + uz * uz;
+            pvf[2] = gx * gx + gy * gy + gz * gz;
         }
         if (rig) {
             v[QP_FRIG] = fx; v[QP_FRIG + 1] = fy; v[QP_FRIG + 2] = fz;
@@ -669,7 +724,7 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
             xr[0] = xi.x; xr[1] = xi.y; xr[2] = xi.z;
         }
         v[QP_FMAX2] = fm;
-        tile_reduce_quench(v, xr, anyrig, D.part + (size_t)t * NPART);
+        tile_reduce_quench(v, pvf, xr, anyrig, D.part + (size_t)t * NPART);
     }
 }
 
@@ -896,10 +951,12 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
             if (mode & MODE_KIN) kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
-            if ((mode & MODE_SCALE) && chain) {
-                v.x *= C.nhc_scale;
-                v.y *= C.nhc_scale;
-                v.z *= C.nhc_scale;
+            if (mode & MODE_SCALE) {
+                if (chain) {
+                    v.x *= C.nhc_scale;
+                    v.y *= C.nhc_scale;
+                    v.z *= C.nhc_scale;
+                }
                 kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
             if (mode & MODE_CLOSE) {
@@ -983,10 +1040,12 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
             if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
-            if ((mode & MODE_SCALE) && chain) {
-                v.x *= C.nhc_scale;
-                v.y *= C.nhc_scale;
-                v.z *= C.nhc_scale;
+            if (mode & MODE_SCALE) {
+                if (chain) {
+                    v.x *= C.nhc_scale;
+                    v.y *= C.nhc_scale;
+                    v.z *= C.nhc_scale;
+                }
                 kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             }
             if (mode & MODE_CLOSE) {
@@ -1373,7 +1432,12 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
             if (!grp_barrier(D, r, nc, epoch)) return;
             for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc) dev_bin(D, t);
             if (!grp_barrier(D, r, nc, epoch)) return;
-            for (int c = me * blockDim.x + threadIdx.x; c < R.ncell; c += nc * blockDim.x) dev_cellsort_one(D, R, c);
+            {
+                const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+                int *buf = reinterpret_cast<int *>(nl_smem) + wib * D.cell_cap;
+                for (int c = me * nwb + wib; c < R.ncell; c += nc * nwb) dev_cellsort_warp(D, R, c, buf);
+                __syncthreads();
+            }
             if (!grp_barrier(D, r, nc, epoch)) return;
             // every CTA has read the flag before the first barrier above
             if (threadIdx.x == 0) {
@@ -1435,7 +1499,7 @@ void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s) {
 void launch_rebuild(const Dev &D, cudaStream_t s) {
     k_cell_clear<<<D.nrep, 256, 0, s>>>(D);
     k_bin<<<D.ntile, nthr(D), 0, s>>>(D);
-    k_cellsort<<<dim3((D.max_cells + 127) / 128, D.nrep), 128, 0, s>>>(D);
+    k_cellsort<<<dim3((D.max_cells + 3) / 4, D.nrep), 128, 4 * D.cell_cap * sizeof(int), s>>>(D);
     k_rebuild_plan<<<1, 32, 0, s>>>(D);
     k_nlist<<<D.nl_grid, 128, nl_smem_bytes(D), s>>>(D);
 }
