@@ -114,6 +114,15 @@ typedef struct {
                                   N_f = dim x mobile atoms                           */
     int pad3_;
     double nhc_tau;            /* chain period tau                                    */
+    int eig_on;                /* 1: Eq. 13 bias, DeltaV_1(sigma) combined with
+                                  DeltaV_2(epsilon) of Eq. 15, epsilon the lowest
+                                  eigenvalue of the Hessian over the allowed motions
+                                  (fixed atoms frozen, rigid layer as one body), by
+                                  Lanczos to a Ritz residual of 1e-10 |epsilon|; 0:
+                                  the slope bias alone.  Per-phase driver only.     */
+    int eig_maxit;             /* Lanczos steps at most (0: 3 n_atoms), capped at the
+                                  dimension of the allowed motions                   */
+    double eig_lo, eig_hi;     /* epsilon_L, epsilon_U of Eq. 15                      */
 } hd_replica_desc;
 
 typedef struct {
@@ -198,6 +207,8 @@ enum {
     HD_OBS_QCONV = 27,         /* 1 if the last quench reached ftol, else 0            */
     HD_OBS_XS = 28,            /* slider x_S of the current configuration             */
     HD_OBS_NHC_E = 29,         /* chain energy sum Q v^2/2 + N_f kT xi_1 + kT sum xi_j */
+    HD_OBS_EIG = 30,           /* epsilon of Eq. 15 (eigenvalue bias)                 */
+    HD_OBS_EIG_ITERS = 31,     /* Lanczos steps of its last evaluation                */
     HD_OBS_LEN = 32
 };
 

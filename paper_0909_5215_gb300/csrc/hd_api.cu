@@ -39,6 +39,9 @@ struct Plan {
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
     size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff;
     size_t o_ctarep, o_pgfirst, o_pgcount, o_boff, o_bj;
+    size_t o_eq, o_ev, o_ew, o_eg, o_ealpha, o_ebeta, o_ey, o_ecoef, o_epart;
+    long long eig_q = 0, eig_t = 0;     // dbl4 entries of all Krylov bases, doubles of all tridiagonals
+    bool any_eig = false;
 };
 
 size_t take(size_t &cur, size_t bytes) {
@@ -57,6 +60,11 @@ bool valid_desc(const hd_replica_desc &d, std::string &why) {
     if (d.n_bonds < 0 || (d.n_bonds > 0 && !d.bonds)) { why = "n_bonds < 0 or NULL bonds"; return false; }
     if (d.nhc_len < 0 || d.nhc_len > 8) { why = "nhc_len must be in [0, 8]"; return false; }
     if (d.nhc_len > 0 && !(d.nhc_tau > 0.0 && std::isfinite(d.nhc_tau))) { why = "nhc_tau must be > 0"; return false; }
+    if (d.eig_on && !(std::isfinite(d.eig_lo) && std::isfinite(d.eig_hi) && d.eig_lo < d.eig_hi)) {
+        why = "the eigenvalue band needs eig_lo < eig_hi";
+        return false;
+    }
+    if (d.eig_maxit < 0) { why = "eig_maxit must be >= 0"; return false; }
     if (d.n_bonds > 0 && !(d.k_bond >= 0.0 && std::isfinite(d.k_bond) && d.r_bond > 0.0 && std::isfinite(d.r_bond))) {
         why = "k_bond must be >= 0 and r_bond > 0";
         return false;
@@ -257,6 +265,24 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
             }
         R.kr_n = nrig > 0 ? d.k_spring / nrig : 0.0;
         R.kr_nf = (float)R.kr_n;
+        // eigenvalue bias: Lanczos steps at most, capped at the dimension of the
+        // allowed motions (dim x mobile atoms, plus dim for the rigid body)
+        R.eig_on = d.eig_on ? 1 : 0;
+        if (R.eig_on) {
+            int nmob = 0;
+            for (int i = 0; i < d.n_atoms; ++i) nmob += d.role[i] == 1;
+            const int dimP = d.dim * nmob + (nrig > 0 ? d.dim : 0);
+            int kmax = d.eig_maxit > 0 ? d.eig_maxit : 3 * d.n_atoms;
+            kmax = std::max(1, std::min(kmax, dimP));
+            R.eig_kmax = kmax;
+            R.eig_lo = d.eig_lo;
+            R.eig_hi = d.eig_hi;
+            R.eig_qoff = P.eig_q;
+            R.eig_toff = P.eig_t;
+            P.eig_q += (long long)(kmax + 1) * d.n_atoms;
+            P.eig_t += kmax;
+            P.any_eig = true;
+        }
         // Nose-Hoover chain masses: Q_1 = N_f kT tau^2, Q_j = kT tau^2
         R.nhc_len = d.nhc_len;
         if (d.nhc_len > 0) {
@@ -363,6 +389,18 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_pgcount = take(cur, R * 4);
     P.o_boff = take(cur, (N + 1) * 4);
     P.o_bj = take(cur, std::max<size_t>(1, P.bond_j.size()) * 4);
+    {
+        const size_t nv = P.any_eig ? N : 1, nq = std::max<long long>(1, P.eig_q), nt = std::max<long long>(1, P.eig_t);
+        P.o_eq = take(cur, nq * sizeof(dbl4));
+        P.o_ev = take(cur, nv * sizeof(dbl4));
+        P.o_ew = take(cur, nv * sizeof(dbl4));
+        P.o_eg = take(cur, nv * sizeof(dbl4));
+        P.o_ealpha = take(cur, nt * 8);
+        P.o_ebeta = take(cur, nt * 8);
+        P.o_ey = take(cur, nt * 8);
+        P.o_ecoef = take(cur, nt * 8);
+        P.o_epart = take(cur, T * 4 * 8);
+    }
     P.bytes = (cur + ALIGN - 1) / ALIGN * ALIGN;
     return true;
 }
@@ -543,6 +581,16 @@ void fill_dev(hd_ctx *c) {
     D.pg_count = at<int>(b, P.o_pgcount);
     D.bond_off = at<int>(b, P.o_boff);
     D.bond_j = at<int>(b, P.o_bj);
+    D.any_eig = P.any_eig ? 1 : 0;
+    D.eq = at<dbl4>(b, P.o_eq);
+    D.ev = at<dbl4>(b, P.o_ev);
+    D.ew = at<dbl4>(b, P.o_ew);
+    D.eg = at<dbl4>(b, P.o_eg);
+    D.ealpha = at<double>(b, P.o_ealpha);
+    D.ebeta = at<double>(b, P.o_ebeta);
+    D.ey = at<double>(b, P.o_ey);
+    D.ecoef = at<double>(b, P.o_ecoef);
+    D.epart = at<double>(b, P.o_epart);
     D.nl_pow2 = 32;
     while (D.nl_pow2 < P.maxnb) D.nl_pow2 <<= 1;
     {
@@ -617,7 +665,9 @@ void queue_step(hd_ctx *c, int mode, std::vector<hd_ctx::Span> *sink) {
     const bool last = !(mode & MODE_OPEN);
     { Timed t(c, sink, T_REBUILD); launch_rebuild(c->D, c->s); }
     { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, last, c->s); }
+    launch_eig(c->D, c->s);
     { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, mode, c->s); }
+    c->launches += c->D.any_eig ? 2 : 0;
     if (!c->D.any_nhc) {
         { Timed t(c, sink, T_UPDATE); launch_update(c->D, mode, c->s); }
         c->launches += 8;
@@ -653,8 +703,9 @@ hd_status refresh_md(hd_ctx *c, bool relist) {
         CK(cudaStreamSynchronize(c->s));
     }
     launch_pair(c->D, false, true, c->s);
+    launch_eig(c->D, c->s);
     launch_scalar(c->D, 0, c->s);
-    c->launches += 2;
+    c->launches += 2 + (c->D.any_eig ? 2 : 0);
     CK(cudaGetLastError());
     return HD_OK;
 }
@@ -671,6 +722,7 @@ bool setup_persistent(hd_ctx *c) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (P.block > 128) return false;  // the persistent kernel is built for tiles of <= 128 atoms
+    if (P.any_eig) return false;      // the eigenvalue bias runs on the per-phase kernels only
     const int bps = persist_blocks_per_sm(c->D);
     const long long maxg = (long long)bps * nsm;
     if (!coop || bps <= 0 || P.nrep > maxg) return false;
@@ -801,11 +853,12 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     launch_init(c->D, d_draw, c->s);
     launch_rebuild(c->D, c->s);
     launch_pair(c->D, false, true, c->s);
+    launch_eig(c->D, c->s);
     launch_scalar(c->D, 0, c->s);
     launch_update(c->D, MODE_KIN, c->s);  // kinetic energy of the initial velocities
     launch_nhc(c->D, MODE_KIN, c->s);     // the chains start from it
     launch_obs(c->D, c->s);
-    c->launches += 11;
+    c->launches += 11 + (c->D.any_eig ? 2 : 0);
     CK(cudaGetLastError());
     c->qdisp.assign(P.nrep, 0.0);
     c->qflag.assign(P.nrep, 0);
@@ -935,7 +988,7 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     }
     CK(cudaGraphLaunch(it->second, c->s));
     if (c->timing) c->graph_pending.push_back(key);
-    c->launches += c->D.any_nhc ? 3 + 10LL * n_steps : 2 + 8LL * n_steps;
+    c->launches += (c->D.any_nhc ? 3 + 10LL * n_steps : 2 + 8LL * n_steps) + (c->D.any_eig ? 2LL * n_steps : 0);
     return HD_OK;
 }
 
@@ -1156,6 +1209,10 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         for (int a = 0; a < 3; ++a) o[HD_OBS_NDV_ZERO + a] = (double)S.n_dv[a];
         o[HD_OBS_QCONV] = c->qconv.empty() ? 0.0 : (double)c->qconv[replica];
         o[HD_OBS_XS] = C.xS;
+        if (R.eig_on) {
+            o[HD_OBS_EIG] = S.eig;
+            o[HD_OBS_EIG_ITERS] = (double)S.eig_iters;
+        }
         if (R.nhc_len > 0) {
             double e = 0.0;
             for (int j = 0; j < R.nhc_len; ++j)

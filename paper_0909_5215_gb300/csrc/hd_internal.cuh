@@ -99,6 +99,11 @@ struct RepDev {
     int nbond;                   // bonds of this replica (0: none; then every pair is LJ)
     int nhc_len;                 // Nose-Hoover chain length (0: Langevin)
     double nhc_nf, nhc_Q[8];     // chain: degrees of freedom, masses
+    // eigenvalue bias (Eq. 13, Eq. 15): band of epsilon, Lanczos steps at most,
+    // offsets of this replica's Krylov basis (dbl4 units) and tridiagonal arrays
+    int eig_on, eig_kmax;
+    double eig_lo, eig_hi;
+    long long eig_qoff, eig_toff;
 };
 
 struct RepState {
@@ -107,6 +112,8 @@ struct RepState {
     long long n_dv[3];           // steps with DeltaV = 0, inside the band, at DeltaV_max
     double nhc_xi[8], nhc_v[8];  // Nose-Hoover chain positions and velocities
     double nhc_k2;               // sum of m v^2 over mobile atoms after the last chain half step
+    double eig;                  // lowest eigenvalue epsilon of the constrained Hessian (Eq. 15)
+    int eig_iters, pad_st;       // Lanczos steps the last evaluation took
     // quench
     double q_dt, q_alpha, q_vb[3], q_fmax, q_disp;
     int q_npos, q_iter, q_done, q_flag;
@@ -121,6 +128,8 @@ struct Scal {
     double q_fbody[3], q_mix, q_alpha, q_dt, q_vb[3];
     int q_zero, q_active;
     double nhc_scale;            // chain: scale of the mobile velocities before the next kick
+    double ce;                   // eigenvalue bias: F_tot += ce grad(epsilon), ce = -dDeltaV/depsilon
+    double dV1, dV2;             // the two terms of Eq. 13
 };
 
 struct Dev {
@@ -153,6 +162,10 @@ struct Dev {
     int fault_rep;               // test hook (-1 off): a CTA of this replica skips one barrier arrival
     int nl_pow2, nl_grid;        // neighbour-row buffer (power of two >= maxnb), k_nlist CTAs
     int any_nhc;                 // some replica runs a Nose-Hoover chain: the update splits around it
+    int any_eig;                 // some replica has the eigenvalue bias
+    dbl4 *eq, *ev, *ew, *eg;     // eigenvalue bias: Krylov bases, eigenvector, work vector, grad epsilon
+    double *ealpha, *ebeta, *ey, *ecoef;  // tridiagonal (alpha, beta), its eigenvector, coefficients
+    double *epart;               // per tile: sum of grad epsilon over rigid atoms (4 doubles)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -311,6 +324,19 @@ __device__ __forceinline__ double warp_max(double v) {
 __device__ __forceinline__ double slider_x(const RepDev &R, long long step, double dt) {
     if (R.v_slide == 0.0) return R.slider[0];
     return R.slider[0] + (double)(step - R.slide_step0) * (R.v_slide * dt);
+}
+
+// Eq. 15: value and derivative of DeltaV_2(epsilon), the shape of Eq. 14 on
+// the band [eps_L, eps_U] of the lowest Hessian eigenvalue.
+__device__ __forceinline__ void dv2(const RepDev &R, double e, double &dv, double &dvp) {
+    if (e >= R.eig_hi) { dv = R.dvmax; dvp = 0.0; return; }
+    if (e <= R.eig_lo) { dv = 0.0; dvp = 0.0; return; }
+    double t = (e - R.eig_hi) / (R.eig_lo - R.eig_hi);
+    double tm1 = 1.0;
+    for (int k = 1; k < R.m_exp; ++k) tm1 *= t;
+    double q = 1.0 - tm1 * t;
+    dv = R.dvmax * q * q;
+    dvp = 2.0 * R.dvmax * q * (-(double)R.m_exp * tm1) / (R.eig_lo - R.eig_hi);
 }
 
 // Eq. 14: value and derivative of DeltaV_1(sigma).

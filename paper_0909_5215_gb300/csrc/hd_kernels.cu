@@ -758,8 +758,21 @@ __device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, do
     if (nr > 0) G += (gs[0] * acc[PART_DRRIG] + gs[1] * acc[PART_DRRIG + 1] + gs[2] * acc[PART_DRRIG + 2]) / (double)nr;
     const double d = sqrt(acc[PART_D2]);
     const double sig = d > 0.0 ? G / d : 0.0;
-    double dV = 0.0, dVp = 0.0;
+    double dV = 0.0, dVp = 0.0, dVe = 0.0, d1 = 0.0, d2 = 0.0;
     if (D.bias_on) dv1(R, sig, dV, dVp);
+    d1 = dV;
+    if (D.bias_on && R.eig_on) {
+        // Eq. 13: DeltaV = DeltaV_1 + DeltaV_2 - DeltaV_1 DeltaV_2 / DeltaV_max
+        double dvp1 = dVp, dvp2 = 0.0;
+        dv2(R, S.eig, d2, dvp2);
+        if (R.dvmax > 0.0) {
+            dV = d1 + d2 - d1 * d2 / R.dvmax;
+            dVp = (1.0 - d2 / R.dvmax) * dvp1;
+            dVe = (1.0 - d1 / R.dvmax) * dvp2;
+        } else {
+            dV = dVp = dVe = 0.0;
+        }
+    }
     const double ca = d > 0.0 ? -dVp / d : 0.0;
     const double cb = d > 0.0 ? dVp * sig / (d * d) : 0.0;
     double fb[3] = {0, 0, 0};
@@ -769,6 +782,17 @@ __device__ void scalar_eval(const Dev &D, int r, int mode, const double *acc, do
             const double srig = d > 0.0 ? (acc[PART_HRIG + a] + grig) / d - sig * acc[PART_DRRIG + a] / (d * d) : 0.0;
             fb[a] = acc[PART_FRIG + a] - gs[a] - dVp * srig;
         }
+    if (dVe != 0.0 && nr > 0) {
+        // the rigid layer's share of -dDeltaV/depsilon grad epsilon, summed per tile
+        for (int a = 0; a < 3; ++a) {
+            double e = 0.0;
+            for (int t = R.tile0; t < R.tile0 + R.ntile; ++t) e += D.epart[(size_t)t * 4 + a];
+            fb[a] -= dVe * e;
+        }
+    }
+    C.ce = -dVe;
+    C.dV1 = d1;
+    C.dV2 = d2;
     double ext = 0.0;
     if (nr > 0) {
         ext = 0.5 * R.kspring * (xT[0] - xs) * (xT[0] - xs);
@@ -945,9 +969,15 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
         if (role == ROLE_MOBILE) {
             const dbl4 F = D.f64[i], H = D.h64[i], dr = D.dr64[i];
             const double ca = C.ca, cb = C.cb;
-            const double Fx = F.x + ca * (H.x - F.x) + cb * dr.x;
-            const double Fy = F.y + ca * (H.y - F.y) + cb * dr.y;
-            const double Fz = F.z + ca * (H.z - F.z) + cb * dr.z;
+            double Fx = F.x + ca * (H.x - F.x) + cb * dr.x;
+            double Fy = F.y + ca * (H.y - F.y) + cb * dr.y;
+            double Fz = F.z + ca * (H.z - F.z) + cb * dr.z;
+            if (C.ce != 0.0) {               // eigenvalue bias (Eq. 13, Eq. 15)
+                const dbl4 g = D.eg[i];
+                Fx += C.ce * g.x;
+                Fy += C.ce * g.y;
+                Fz += C.ce * g.z;
+            }
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
             if (mode & MODE_KIN) kin = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
@@ -1034,9 +1064,15 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
         if (role == ROLE_MOBILE) {
             const float4 F = D.f32[i], H = D.h32[i], dr = ai.d;
             const float ca = (float)C.ca, cb = (float)C.cb;
-            const double Fx = (double)fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
-            const double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
-            const double Fz = (double)fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
+            double Fx = (double)fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
+            double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
+            double Fz = (double)fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
+            if (C.ce != 0.0) {               // eigenvalue bias (Eq. 13, Eq. 15), FP64
+                const dbl4 g = D.eg[i];
+                Fx += C.ce * g.x;
+                Fy += C.ce * g.y;
+                Fz += C.ce * g.z;
+            }
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
             if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));

@@ -15,6 +15,7 @@ void launch_scalar(const Dev &D, int mode, cudaStream_t s);
 void launch_update(const Dev &D, int mode, cudaStream_t s);
 void launch_obs(const Dev &D, cudaStream_t s);
 void launch_nhc(const Dev &D, int mode, cudaStream_t s);          // the chain between two kicks, per replica
+void launch_eig(const Dev &D, cudaStream_t s);                    // epsilon (Lanczos) and grad epsilon (hd_eig.cu)
 void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s);
 void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 6 kernels
 void launch_qdisp(const Dev &Q, cudaStream_t s);

@@ -25,7 +25,7 @@ HD_DRIVER_AUTO, HD_DRIVER_KERNELS, HD_DRIVER_PERSISTENT = 0, 1, 2
 OBS_FIELDS = ["step", "t_md", "t_h", "V", "K", "dV", "sigma", "d", "F_R", "x_T", "y_T", "z_T",
               "n_rebuild", "boost", "q_iter", "q_fmax", "G", "fbody_x", "fbody_y", "fbody_z",
               "vbody_x", "vbody_y", "vbody_z", "q_disp", "n_dv_zero", "n_dv_band", "n_dv_max", "q_conv",
-              "x_S", "nhc_energy", "reserved30", "reserved31"]
+              "x_S", "nhc_energy", "eig", "eig_iters"]
 OBS_LEN = 32
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_NOMEM", 4: "HD_ERR_NUMERIC",
                 5: "HD_ERR_TIMEOUT", 6: "HD_ERR_STATE", 7: "HD_ERR_UNIMPLEMENTED", 8: "HD_ERR_OVERFLOW"}
@@ -52,6 +52,7 @@ class hd_replica_desc(C.Structure):
         ("n_bonds", C.c_int), ("pad2_", C.c_int), ("bonds", C.POINTER(C.c_int32)),
         ("k_bond", C.c_double), ("r_bond", C.c_double),
         ("nhc_len", C.c_int), ("pad3_", C.c_int), ("nhc_tau", C.c_double),
+        ("eig_on", C.c_int), ("eig_maxit", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
     ]
 
 
@@ -180,12 +181,7 @@ def make_params(params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, pre
 
 
 def make_descs(reps):
-    """Build the C descriptors; returns (array, keep-alive list).  Replicas
-    asking for what the library does not compute (the eigenvalue bias of
-    Eq. 13/15) are refused rather than run without it."""
-    for k, r in enumerate(reps):
-        if getattr(r, "eig_on", 0):
-            raise HdError(HD_ERR_UNIMPLEMENTED, "replica %d: the eigenvalue bias is not implemented on the GPU" % k)
+    """Build the C descriptors; returns (array, keep-alive list)."""
     keep = []
     arr = (hd_replica_desc * len(reps))()
 
@@ -227,6 +223,9 @@ def make_descs(reps):
             d.k_bond, d.r_bond = float(r.k_bond), float(r.r_bond)
         d.nhc_len = int(getattr(r, "nhc_len", 0))
         d.nhc_tau = float(getattr(r, "nhc_tau", 0.5))
+        d.eig_on = int(getattr(r, "eig_on", 0))
+        d.eig_maxit = int(getattr(r, "eig_maxit", 0))
+        d.eig_lo, d.eig_hi = float(getattr(r, "eig_lo", 0.0)), float(getattr(r, "eig_hi", 1.0))
     return arr, keep
 
 

@@ -161,17 +161,19 @@ def test_binding_fails_loudly_without_library(hdlib, monkeypatch):
         hdlib.lib()
 
 
-def test_eigenvalue_bias_is_refused_not_dropped():
-    """The library computes the slope bias only: a replica asking for the
-    eigenvalue term is refused before anything reaches the device."""
+def test_eigenvalue_bias_reaches_the_descriptor(hdlib):
+    """The eigenvalue bias (Eq. 13, Eq. 15) is carried into the C descriptor;
+    a band with eig_lo >= eig_hi is refused on the host."""
     from conftest import small2d
-    from paper_0909_5215_gb300 import hd
+    from paper_0909_5215_gb300 import model as M
     r = small2d()
-    r.eig_on = 1
-    with pytest.raises(hd.HdError) as ei:
-        hd.make_descs([r])
-    assert ei.value.status == hd.HD_ERR_UNIMPLEMENTED
-    hd.make_descs([small2d()])
+    r.eig_on, r.eig_lo, r.eig_hi, r.eig_maxit = 1, 0.5, 2.0, 300
+    descs, _keep = hdlib.make_descs([r])
+    assert descs[0].eig_on == 1 and descs[0].eig_lo == 0.5 and descs[0].eig_hi == 2.0 and descs[0].eig_maxit == 300
+    assert hdlib.hd_workspace_bytes(descs, 1, hdlib.make_params(M.Params(bias_on=1))) > 0
+    r.eig_lo = 3.0
+    descs, _keep = hdlib.make_descs([r])
+    assert hdlib.hd_workspace_bytes(descs, 1, hdlib.make_params(M.Params(bias_on=1))) == 0
 
 
 def test_continuous_sliding_reaches_the_descriptor():

@@ -153,3 +153,77 @@ def test_nose_hoover_chain_matches_oracle(hd, oracle_mod, prec, driver):
         if reps[k].nhc_len:
             assert ob["nhc_energy"] == pytest.approx(o.nhc_energy(), rel=1e-9 if prec == 0 else 1e-4, abs=1e-12)
     b.close()
+
+
+def _both_active(oracle_mod, mk, seed):
+    """An equilibrated model (quench, then Langevin MD) with sigma and epsilon
+    both inside their bands (the eigenvalue bias of Eq. 13 and Eq. 15)."""
+    from paper_0909_5215_gb300 import model as M
+    base = mk()
+    o = oracle_mod.OracleReplica(base, M.Params())
+    xq, _, _ = o.quench(method=1, ftol=1e-8, max_iter=20000)
+    r = base.copy()
+    r.pos, r.pos_ref, r.rep_id = xq.copy(), xq.copy(), seed
+    o = oracle_mod.OracleReplica(r, M.Params())
+    o.run(1000)
+    r.pos, r.vel = o.x.copy(), o.v.copy()
+    o = oracle_mod.OracleReplica(r, M.Params(bias_on=1))
+    s0 = o.s.sigma
+    e0, _ = o.lowest_eig()
+    r.dvmax, r.m_exp, r.eig_on = 0.3, 2, 1
+    r.sig_lo, r.sig_hi = s0 - 0.5 * abs(s0) - 0.1, s0 + 0.5 * abs(s0) + 0.1
+    r.eig_lo, r.eig_hi = e0 - 0.5 * abs(e0) - 0.05, e0 + 0.5 * abs(e0) + 0.05
+    return r
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eigenvalue_bias_matches_oracle(hd, oracle_mod, prec):
+    """Eq. 13 with DeltaV_2(epsilon) of Eq. 15: epsilon from Lanczos on the
+    constrained Hessian, its gradient from phi''', in a batch with a plain
+    slope-bias replica.  Both sides stop Lanczos at a Ritz residual of
+    1e-10 |epsilon| (the GPU reorthogonalises by two passes of classical
+    Gram-Schmidt where the oracle uses modified Gram-Schmidt), so epsilon
+    agrees to ~1e-10 and the eigenvector, which enters the force through
+    grad epsilon, to ~1e-10 over the spectral gap.  Tolerances: epsilon and
+    DeltaV relative 1e-9 (FP64 form) / 1e-6 (split form) at the start and after
+    30 steps; positions 1e-8 / 1e-4."""
+    from paper_0909_5215_gb300 import model as M
+    reps = [_both_active(oracle_mod, small2d, seed=11), _both_active(oracle_mod, small3d, seed=12)]
+    plain = reps[0].copy()
+    plain.eig_on, plain.rep_id = 0, 13
+    reps.append(plain)
+    p = M.Params(prec=prec, bias_on=1)
+    b = hd.Batch(reps, p)
+    ors = [oracle_mod.OracleReplica(r, p) for r in reps]
+    rel = 1e-9 if prec == 0 else 1e-6
+    for k, o in enumerate(ors):
+        ob = b.obs(k)
+        if reps[k].eig_on:
+            assert 0.0 < o.s.dV2 < 0.3 and o.s.dVe != 0.0
+            assert ob["eig"] == pytest.approx(o.s.eig, rel=1e-9)
+            assert ob["eig_iters"] > 10
+        assert ob["dV"] == pytest.approx(o.s.dV, rel=rel)
+    th0 = [o.s.t_h for o in ors]
+    b.step(30)
+    oracle_mod.run_batch(ors, 30)
+    for k, o in enumerate(ors):
+        ob = b.obs(k)
+        if reps[k].eig_on:
+            assert ob["eig"] == pytest.approx(o.s.eig, rel=rel)
+        assert ob["dV"] == pytest.approx(o.s.dV, rel=rel, abs=1e-12)
+        assert ob["t_h"] - th0[k] == pytest.approx(o.s.t_h - th0[k], rel=rel)
+        assert np.abs(b.positions(k) - o.x).max() < (1e-8 if prec == 0 else 1e-4)
+    b.close()
+
+
+def test_eigenvalue_bias_keeps_the_per_phase_driver(hd, oracle_mod):
+    """A batch with the eigenvalue bias asks for the persistent driver and
+    gets the per-phase kernels (the Lanczos runs one CTA per replica)."""
+    from paper_0909_5215_gb300 import model as M
+    r = thermalise(small2d(), amp=0.03, seed=61)
+    r.eig_on, r.eig_lo, r.eig_hi, r.dvmax = 1, -1.0, 1.0, 0.2
+    b = hd.Batch([r], M.Params(prec=1, bias_on=1), driver=hd.HD_DRIVER_PERSISTENT)
+    assert b.info()["driver"] == hd.HD_DRIVER_KERNELS
+    b.step(5)
+    b.sync()
+    b.close()
