@@ -402,7 +402,9 @@ def run_ours(args):
         # the persistent launch has no separate pair kernel to time
         roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
                 "kernel": "k_persist (phases fused; no per-phase timing)", "mean_neighbours": nnb}
-    phases = {k: tim[k] for k in tim}
+    phases = {k: tim[k] for k in tim if not k.startswith("reserved")}
+    phases["rebuild_ms"] = tim["rebuild_prep_ms"] + tim["nlist_ms"]
+    phases["rebuild_share_of_md"] = phases["rebuild_ms"] / md_ms if md_ms > 0 else None
 
     # ---- FP64 form on the same equilibrated window: a batch in the plain form
     # created from this batch's current state (positions, velocities, r_O,

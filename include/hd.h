@@ -226,9 +226,12 @@ hd_status hd_info(const hd_ctx *ctx, int64_t out[12]);
  * captured CUDA graph they are event nodes.  enable: 1 start timing, 0 stop,
  * 2 zero the totals, -1 leave as is.  out (may be NULL) receives, in ms and
  * counts since the last reset: [0] pair ms, [1] pair launches, [2] update ms,
- * [3] update launches, [4] list-rebuild ms, [5] rebuild passes,
- * [6] scalar ms, [7] scalar launches.  Synchronises the stream. */
-hd_status hd_timing(hd_ctx *ctx, int enable, double out[8]);
+ * [3] update launches, [4] list-rebuild preparation ms (plan, cell clear,
+ * binning, cell sort), [5] its passes, [6] scalar ms, [7] scalar launches,
+ * [8] row-build (k_nlist) ms, [9] its launches, [10] eigenvalue-bias ms
+ * (Lanczos and grad epsilon), [11] its passes, [12..15] reserved (0).
+ * Synchronises the stream. */
+hd_status hd_timing(hd_ctx *ctx, int enable, double out[16]);
 
 /* Neighbour list of one replica without any device allocation.  For callers
  * that must not let a library allocate device memory: a program that

@@ -37,7 +37,7 @@ struct Plan {
     size_t o_rep, o_st, o_sc, o_trep, o_tstart, o_tn, o_part, o_qpart, o_kpart;
     size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
-    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff;
+    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff, o_rbaoff, o_rblist, o_rbmeta;
     size_t o_ctarep, o_pgfirst, o_pgcount, o_boff, o_bj;
     size_t o_eq, o_ev, o_ew, o_eg, o_ealpha, o_ebeta, o_ey, o_ecoef, o_epart;
     long long eig_q = 0, eig_t = 0;     // dbl4 entries of all Krylov bases, doubles of all tridiagonals
@@ -384,6 +384,9 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_adopt = take(cur, R * 4);
     P.o_orig = take(cur, N * 4);
     P.o_rboff = take(cur, (R + 1) * 4);
+    P.o_rbaoff = take(cur, (R + 1) * 4);
+    P.o_rblist = take(cur, R * 4);
+    P.o_rbmeta = take(cur, 4 * 4);
     P.o_ctarep = take(cur, T * 4);       // at most one CTA per tile
     P.o_pgfirst = take(cur, R * 4);
     P.o_pgcount = take(cur, R * 4);
@@ -431,8 +434,8 @@ struct hd_ctx {
     std::vector<Span> pending;            // recorded directly on the stream
     std::map<int, std::vector<Span>> graph_spans;  // event nodes inside graph n
     std::vector<int> graph_pending;       // graphs launched, spans not yet harvested
-    double tsum[4] = {0, 0, 0, 0};
-    long long tcnt[4] = {0, 0, 0, 0};
+    double tsum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long tcnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<cudaEvent_t> free_events;
 };
 
@@ -461,7 +464,7 @@ hd_status fail(hd_ctx *c, hd_status st, const char *fmt, ...) {
 template <typename T>
 T *at(char *base, size_t off) { return reinterpret_cast<T *>(base + off); }
 
-enum { T_PAIR = 0, T_UPDATE = 1, T_REBUILD = 2, T_SCALAR = 3 };
+enum { T_PAIR = 0, T_UPDATE = 1, T_REBUILD = 2, T_SCALAR = 3, T_NLIST = 4, T_EIG = 5, T_NCAT = 8 };
 
 cudaEvent_t get_event(hd_ctx *c) {
     if (!c->free_events.empty()) {
@@ -573,6 +576,9 @@ void fill_dev(hd_ctx *c) {
     D.qdisp = at<unsigned long long>(b, P.o_qdisp);
     D.orig = at<int>(b, P.o_orig);
     D.rb_off = at<int>(b, P.o_rboff);
+    D.rb_aoff = at<int>(b, P.o_rbaoff);
+    D.rb_list = at<int>(b, P.o_rblist);
+    D.rb_meta = at<int>(b, P.o_rbmeta);
     D.cta_rep = at<int>(b, P.o_ctarep);
     // test hook for the barrier time-out path: HD_TEST_SKIP_ARRIVE=<replica>
     D.fault_rep = -1;
@@ -663,9 +669,10 @@ hd_status upload_reps(hd_ctx *c) {
 void queue_step(hd_ctx *c, int mode, std::vector<hd_ctx::Span> *sink) {
     // per-atom energies are observables only: computed on the last step of a call
     const bool last = !(mode & MODE_OPEN);
-    { Timed t(c, sink, T_REBUILD); launch_rebuild(c->D, c->s); }
+    { Timed t(c, sink, T_REBUILD); launch_rebuild_prep(c->D, c->s); }
+    { Timed t(c, sink, T_NLIST); launch_nlist(c->D, c->s); }
     { Timed t(c, sink, T_PAIR); launch_pair(c->D, false, last, c->s); }
-    launch_eig(c->D, c->s);
+    if (c->D.any_eig) { Timed t(c, sink, T_EIG); launch_eig(c->D, c->s); }
     { Timed t(c, sink, T_SCALAR); launch_scalar(c->D, mode, c->s); }
     c->launches += c->D.any_eig ? 2 : 0;
     if (!c->D.any_nhc) {
@@ -1250,17 +1257,17 @@ hd_status hd_sync(hd_ctx *c) {
     return check_device(c);
 }
 
-hd_status hd_timing(hd_ctx *c, int enable, double out[8]) {
+hd_status hd_timing(hd_ctx *c, int enable, double out[16]) {
     if (!c) return HD_ERR_ARG;
     if (enable < -1 || enable > 2) return fail(c, HD_ERR_ARG, "timing mode %d", enable);
     harvest_all(c);
     if (enable == 2) {
-        for (int k = 0; k < 4; ++k) { c->tsum[k] = 0.0; c->tcnt[k] = 0; }
+        for (int k = 0; k < T_NCAT; ++k) { c->tsum[k] = 0.0; c->tcnt[k] = 0; }
     } else if (enable >= 0) {
         c->timing = enable;
     }
     if (out)
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < T_NCAT; ++k) {
             out[2 * k] = c->tsum[k];
             out[2 * k + 1] = (double)c->tcnt[k];
         }

@@ -155,7 +155,9 @@ struct Dev {
     unsigned int *bar;           // per replica barrier counters (persistent driver)
     unsigned long long *qdisp;   // per replica max |x_q - r_O|^2 (bits of the double)
     const int *orig;             // per slot: index of the atom in its replica's input
-    int *rb_off;                 // [nrep + 1] compacted atom offsets of rebuilding replicas
+    int *rb_list;                // replicas whose list is rebuilt, ascending (count rb_meta[0])
+    int *rb_off, *rb_aoff;       // [count + 1] first compacted cell / atom of each of them
+    int *rb_meta;                // {count, compacted cells, compacted atoms}
     const int *cta_rep;          // persistent launch: replica of each CTA (-1: spare)
     const int *pg_first, *pg_count;  // persistent launch: first CTA and CTA count of each replica
     const int *bond_off, *bond_j;    // per slot: bond partners (slots) in bond_j[bond_off[i] .. bond_off[i+1])

@@ -148,17 +148,69 @@ __global__ void k_init(Dev D, const int *draw_vel) {
 }
 
 // ---------------------------------------------------------------- neighbour list
-__global__ void k_cell_clear(Dev D) {
-    const int r = blockIdx.x;
-    if (!D.rebuild[r]) return;
-    const RepDev &R = D.rep[r];
-    for (int c = threadIdx.x; c < R.ncell; c += blockDim.x) D.cell_cnt[R.cell0 + c] = 0;
+// A list rebuild touches only the replicas whose flag is set.  k_rebuild_plan
+// (one warp) compacts them: rb_list[k] is the k-th such replica in ascending
+// order, rb_off[k] / rb_aoff[k] its first cell / atom in the compacted range,
+// rb_meta = {count, cells, atoms}.  The other rebuild kernels run fixed grids
+// that stride over that compacted range, so a step without rebuilds costs a
+// few near-empty launches.
+__global__ void k_rebuild_plan(Dev D) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
+    int nrb = 0, coff = 0, aoff = 0;
+    for (int base = 0; base < D.nrep; base += 32) {
+        const int r = base + lane;
+        const bool f = r < D.nrep && D.rebuild[r] != 0;
+        const int nc = f ? D.rep[r].ncell : 0, na = f ? D.rep[r].n : 0;
+        int c = nc, a = na;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int tc = __shfl_up_sync(full, c, o), ta = __shfl_up_sync(full, a, o);
+            if (lane >= o) {
+                c += tc;
+                a += ta;
+            }
+        }
+        const unsigned m = __ballot_sync(full, f);
+        if (f) {
+            const int k = nrb + __popc(m & ((1u << lane) - 1u));
+            D.rb_list[k] = r;
+            D.rb_off[k] = coff + c - nc;
+            D.rb_aoff[k] = aoff + a - na;
+        }
+        nrb += __popc(m);
+        coff += __shfl_sync(full, c, 31);
+        aoff += __shfl_sync(full, a, 31);
+    }
+    if (lane == 0) {
+        D.rb_off[nrb] = coff;
+        D.rb_aoff[nrb] = aoff;
+        D.rb_meta[0] = nrb;
+        D.rb_meta[1] = coff;
+        D.rb_meta[2] = aoff;
+    }
 }
 
-__device__ __forceinline__ void dev_bin(const Dev &D, int t) {
-    const int r = D.tile_rep[t];
-    if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
-    const int i = D.tile_start[t] + threadIdx.x;
+// Entry k of the compacted replicas that holds compacted index idx.
+__device__ __forceinline__ int rb_find(const int *off, int n, int idx) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_cell_clear(Dev D) {
+    const int n = D.rb_meta[0], total = D.rb_meta[1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int k = rb_find(D.rb_off, n, idx);
+        D.cell_cnt[D.rep[D.rb_list[k]].cell0 + idx - D.rb_off[k]] = 0;
+    }
+}
+
+__device__ __forceinline__ void dev_bin_atom(const Dev &D, int r, int i) {
     const RepDev &R = D.rep[r];
     const int4 p = D.rec[i].p;
     const dbl4 x = D.x[i];
@@ -170,7 +222,21 @@ __device__ __forceinline__ void dev_bin(const Dev &D, int t) {
     else set_err(D, HD_ERR_OVERFLOW, i, r);
     D.pfixb[i] = p;
 }
-__global__ void k_bin(Dev D) { dev_bin(D, blockIdx.x); }
+// tile form, for the persistent driver (which rebuilds one replica at a time)
+__device__ __forceinline__ void dev_bin(const Dev &D, int t) {
+    const int r = D.tile_rep[t];
+    if (!D.rebuild[r] || threadIdx.x >= D.tile_n[t]) return;
+    dev_bin_atom(D, r, D.tile_start[t] + threadIdx.x);
+}
+__global__ void k_bin(Dev D) {
+    const int n = D.rb_meta[0], total = D.rb_meta[2];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int k = rb_find(D.rb_aoff, n, idx);
+        const int r = D.rb_list[k];
+        dev_bin_atom(D, r, D.rep[r].atom0 + idx - D.rb_aoff[k]);
+    }
+}
+
 
 // Each cell's atom list in ascending slot order: one warp per cell copies the
 // list to shared memory and writes every entry at its rank (slot indices are
@@ -192,24 +258,12 @@ __device__ __forceinline__ void dev_cellsort_warp(const Dev &D, const RepDev &R,
 }
 __global__ void __launch_bounds__(128) k_cellsort(Dev D) {
     extern __shared__ int cs_buf[];
-    const int r = blockIdx.y;
-    if (!D.rebuild[r]) return;
-    const RepDev &R = D.rep[r];
-    const int w = threadIdx.x >> 5;
-    const int c = blockIdx.x * (blockDim.x >> 5) + w;
-    if (c < R.ncell) dev_cellsort_warp(D, R, c, cs_buf + w * D.cell_cap);
-}
-
-// Prefix of the cell counts of the replicas whose rebuild flag is set:
-// rb_off[r] = first compacted cell of replica r, rb_off[nrep] = total.
-__global__ void k_rebuild_plan(Dev D) {
-    if (threadIdx.x != 0) return;
-    int tot = 0;
-    for (int r = 0; r < D.nrep; ++r) {
-        D.rb_off[r] = tot;
-        if (D.rebuild[r]) tot += D.rep[r].ncell;
+    const int w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const int n = D.rb_meta[0], total = D.rb_meta[1];
+    for (int idx = blockIdx.x * nwb + w; idx < total; idx += gridDim.x * nwb) {
+        const int k = rb_find(D.rb_off, n, idx);
+        dev_cellsort_warp(D, D.rep[D.rb_list[k]], idx - D.rb_off[k], cs_buf + w * D.cell_cap);
     }
-    D.rb_off[D.nrep] = tot;
 }
 
 // Row i = every j != i whose FP64 minimum-image squared distance is below
@@ -406,15 +460,10 @@ __global__ void __launch_bounds__(128) k_nlist(Dev D) {
     int *sj;
     unsigned char *scls;
     nl_smem_carve(D, nl_smem, sp, sj, scls);
-    const int total = D.rb_off[D.nrep];
+    const int n = D.rb_meta[0], total = D.rb_meta[1];
     for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
-        int lo = 0, hi = D.nrep - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (D.rb_off[mid] <= idx) lo = mid;
-            else hi = mid - 1;
-        }
-        dev_nlist_cell(D, lo, idx - D.rb_off[lo], M, sp, sj, scls);
+        const int k = rb_find(D.rb_off, n, idx);
+        dev_nlist_cell(D, D.rb_list[k], idx - D.rb_off[k], M, sp, sj, scls);
     }
 }
 
@@ -541,6 +590,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// 1/x to FP32 rounding: the hardware approximation refined by one Newton
+// step, y (2 - x y), so that its error carries no bias into the forces
+// (an unrefined approximation shifts every pair force the same way, and the
+// slope sigma of Eq. 5 sums them over the whole replica).
+__device__ __forceinline__ float rcp_refined(float x) {
+    const float y = rcp_approx(x);
+    return fmaf(y, fmaf(-x, y, 1.f), y);
+}
 
 template <bool Q, bool E>
 __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
@@ -561,6 +618,7 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const float q0h = R.r0sq_hi[ti][0], q1h = R.r0sq_hi[ti][1];
     const float q0l = R.r0sq_lo[ti][0], q1l = R.r0sq_lo[ti][1];
     const bool exact = R.exact_r2 != 0;
+    const float r2corr = exact ? 2.f * R.lsb_rel[0] : 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
     const int nn = act ? D.nnb[i] : 0;
     const int *nb = D.nbr + i;
@@ -580,12 +638,15 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     auto term = [&](const AtomRec &aj, int ix, int iy, int iz, float dx, float dy, float dz, float r2) {
         const int tj = aj.p.w & 1;
         const float r0h = tj ? q1h : q0h, r0l = tj ? q1l : q0l;
-        float ir2 = rcp_approx(r2);
-        float tt = ((r0h - r2) + r0l) * ir2;
+        // the FP32 r^2 with the rounding of the fixed-point unit undone (all
+        // axes share its relative rounding when they share the unit)
+        const float r2c = fmaf(r2, r2corr, r2);
+        float ir2 = rcp_refined(r2c);
+        float tt = ((r0h - r2c) + r0l) * ir2;
         if (exact && fabsf(tt) < 0.25f) {
             float r2h, r2l;
             r2_split(R, ix, iy, iz, r2h, r2l);
-            ir2 = rcp_approx(r2h);
+            ir2 = rcp_refined(r2h);
             tt = ((r0h - r2h) + (r0l - r2l)) * ir2;
         }
         const float u = 1.f + tt;
@@ -1532,12 +1593,16 @@ cudaError_t nl_configure(const Dev &D) {
 void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s) {
     k_init<<<D.ntile, nthr(D), 0, s>>>(D, draw_vel);
 }
-void launch_rebuild(const Dev &D, cudaStream_t s) {
-    k_cell_clear<<<D.nrep, 256, 0, s>>>(D);
-    k_bin<<<D.ntile, nthr(D), 0, s>>>(D);
-    k_cellsort<<<dim3((D.max_cells + 3) / 4, D.nrep), 128, 4 * D.cell_cap * sizeof(int), s>>>(D);
+void launch_rebuild_prep(const Dev &D, cudaStream_t s) {
     k_rebuild_plan<<<1, 32, 0, s>>>(D);
-    k_nlist<<<D.nl_grid, 128, nl_smem_bytes(D), s>>>(D);
+    k_cell_clear<<<D.nl_grid, 256, 0, s>>>(D);
+    k_bin<<<D.nl_grid, 256, 0, s>>>(D);
+    k_cellsort<<<D.nl_grid, 128, 4 * D.cell_cap * sizeof(int), s>>>(D);
+}
+void launch_nlist(const Dev &D, cudaStream_t s) { k_nlist<<<D.nl_grid, 128, nl_smem_bytes(D), s>>>(D); }
+void launch_rebuild(const Dev &D, cudaStream_t s) {
+    launch_rebuild_prep(D, s);
+    launch_nlist(D, s);
 }
 void launch_pair(const Dev &D, bool quench, bool energy, cudaStream_t s) {
     if (D.prec == HD_FP64) {

@@ -9,6 +9,8 @@ namespace hd {
 
 void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s);
 void launch_rebuild(const Dev &D, cudaStream_t s);            // 5 kernels, flag-gated per replica
+void launch_rebuild_prep(const Dev &D, cudaStream_t s);       // the first 4: plan, clear, bin, cell sort
+void launch_nlist(const Dev &D, cudaStream_t s);              // the 5th: rows from the cells
 // energy: also compute per-atom LJ energies (observables only; not needed by the dynamics)
 void launch_pair(const Dev &D, bool quench, bool energy, cudaStream_t s);
 void launch_scalar(const Dev &D, int mode, cudaStream_t s);

@@ -66,8 +66,9 @@ SYMBOLS = ["hd_workspace_bytes", "hd_create", "hd_set_slider", "hd_set_bias", "h
            "hd_read", "hd_info", "hd_timing", "hd_nlist_static", "hd_sync", "hd_destroy", "hd_last_error"]
 INFO_FIELDS = ["n_rep", "natom", "maxnb", "cell_cap", "ntile", "driver", "persistent_ctas", "launches",
                "h2d_bytes", "d2h_bytes", "workspace_bytes", "reserved"]
-TIMING_FIELDS = ["pair_ms", "pair_launches", "update_ms", "update_launches", "rebuild_ms", "rebuild_passes",
-                 "scalar_ms", "scalar_launches"]
+TIMING_FIELDS = ["pair_ms", "pair_launches", "update_ms", "update_launches", "rebuild_prep_ms", "rebuild_passes",
+                 "scalar_ms", "scalar_launches", "nlist_ms", "nlist_launches", "eig_ms", "eig_passes",
+                 "reserved12", "reserved13", "reserved14", "reserved15"]
 _lib = None
 
 
@@ -148,7 +149,7 @@ def hd_info(ctx):
 
 
 def hd_timing(ctx, enable):
-    out = (C.c_double * 8)()
+    out = (C.c_double * 16)()
     st = lib().hd_timing(ctx, int(enable), out)
     return st, list(out)
 
