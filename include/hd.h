@@ -134,6 +134,10 @@ typedef struct {
     uint64_t seed;             /* Philox key                                          */
     int maxnb;                 /* neighbour row capacity (0: 32 if all 2-D, else 112) */
     int cell_cap;              /* atoms per cell capacity (0: from the input)         */
+    int pair_kernel;           /* split form, per-phase driver: 0 the scalar pair
+                                  sweep, 1 the packed FP32x2 one (two list entries a
+                                  thread per instruction; tiles of <= 128 atoms)      */
+    int pad_;
 } hd_params;
 
 /* Bytes of device workspace hd_create needs for this batch.  Returns 0 if

@@ -1,9 +1,11 @@
-"""Autotuner: pick the driver and tile size of a batch by timing them.
+"""Autotuner: pick the driver, tile size and pair-sweep variant of a batch
+by timing them.
 
 For a batch signature (replica sizes, dimensions, precision) each candidate
-(driver in {per-phase kernels, persistent}, tile size in {64, 128, 256}) is
-created on a scratch copy of the replicas, stepped `warm` steps untimed and
-`steps` steps timed with CUDA events; the fastest wins.  Results are kept in
+(driver in {per-phase kernels, persistent}, tile size in {64, 128, 256},
+and for the split form's per-phase kernels the scalar or the packed FP32x2
+pair sweep) is created on a scratch copy of the replicas, stepped `warm`
+steps untimed and `steps` steps timed with CUDA events; the fastest wins.  Results are kept in
 a JSON cache keyed by the signature (with the library build and the GPU
 model), so a workload is tuned once per build and device.
 """
@@ -15,8 +17,16 @@ import os
 
 from . import hd
 
-CANDIDATES = [(hd.HD_DRIVER_KERNELS, 128), (hd.HD_DRIVER_KERNELS, 64), (hd.HD_DRIVER_KERNELS, 256),
-              (hd.HD_DRIVER_PERSISTENT, 128), (hd.HD_DRIVER_PERSISTENT, 64)]
+# (driver, tile size, pair-sweep variant: 0 scalar, 1 packed FP32x2)
+CANDIDATES = [(hd.HD_DRIVER_KERNELS, 128, 0), (hd.HD_DRIVER_KERNELS, 64, 0), (hd.HD_DRIVER_KERNELS, 256, 0),
+              (hd.HD_DRIVER_KERNELS, 128, 1), (hd.HD_DRIVER_KERNELS, 64, 1),
+              (hd.HD_DRIVER_PERSISTENT, 128, 0), (hd.HD_DRIVER_PERSISTENT, 64, 0)]
+DEFAULT = (hd.HD_DRIVER_KERNELS, 128, 0)
+
+
+def candidates(params):
+    """The packed pair sweep exists in the split form only."""
+    return [c for c in CANDIDATES if c[2] == 0 or params.prec == hd.HD_FP32_SPLIT]
 
 
 def build_identity() -> str:
@@ -69,17 +79,18 @@ def save(path, table):
 
 
 def choose(timings):
-    """timings: {(driver, block): ms per step or None}; the fastest measured one."""
+    """timings: {(driver, block, pair_kernel): ms per step or None}; the
+    fastest measured one."""
     ok = {k: v for k, v in timings.items() if v is not None}
     if not ok:
-        return (hd.HD_DRIVER_KERNELS, 128)
+        return DEFAULT
     return min(ok, key=lambda k: (ok[k], k))
 
 
-def time_candidate(reps, params, driver, block, steps=100, warm=20):
+def time_candidate(reps, params, driver, block, steps=100, warm=20, pair_kernel=0):
     import torch
     try:
-        b = hd.Batch(reps, params, driver=driver, block=block)
+        b = hd.Batch(reps, params, driver=driver, block=block, pair_kernel=pair_kernel)
     except hd.HdError:
         return None
     if driver == hd.HD_DRIVER_PERSISTENT and b.info()["driver"] != hd.HD_DRIVER_PERSISTENT:
@@ -99,16 +110,18 @@ def time_candidate(reps, params, driver, block, steps=100, warm=20):
 
 
 def tune(reps, params, cache=None, steps=100, warm=20, timer=time_candidate):
-    """Return (driver, block, timings) for this batch, measuring on a miss."""
+    """Return (driver, block, pair_kernel, timings) for this batch, measuring
+    on a miss."""
     path = cache or default_cache()
     key = signature(reps, params, build_identity())
     table = load(path)
-    if key in table:
+    if key in table and "pair_kernel" in table[key]:
         e = table[key]
-        return e["driver"], e["block"], e.get("ms", {})
+        return e["driver"], e["block"], e["pair_kernel"], e.get("ms", {})
     scratch = [r.copy() for r in reps]
-    timings = {c: timer(scratch, params, c[0], c[1], steps, warm) for c in CANDIDATES}
-    drv, blk = choose(timings)
-    table[key] = {"driver": drv, "block": blk, "ms": {"%d/%d" % k: v for k, v in timings.items()}}
+    timings = {c: timer(scratch, params, c[0], c[1], steps, warm, c[2]) for c in candidates(params)}
+    drv, blk, pk = choose(timings)
+    table[key] = {"driver": drv, "block": blk, "pair_kernel": pk,
+                  "ms": {"%d/%d/%d" % k: v for k, v in timings.items()}}
     save(path, table)
-    return drv, blk, table[key]["ms"]
+    return drv, blk, pk, table[key]["ms"]

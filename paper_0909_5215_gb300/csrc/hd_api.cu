@@ -94,6 +94,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     if (p->prec != HD_FP64 && p->prec != HD_FP32_SPLIT) { why = "prec must be HD_FP64 or HD_FP32_SPLIT"; return false; }
     if (!(p->dt > 0.0) || !(p->rc > 0.0) || !(p->skin > 0.0)) { why = "dt, rc and skin must be > 0"; return false; }
     P.block = p->block > 0 ? p->block : 128;
+    if (p->pair_kernel < 0 || p->pair_kernel > 1) { why = "pair_kernel must be 0 or 1"; return false; }
     if (P.block % 32 != 0 || P.block > 256) { why = "block must be a multiple of 32, at most 256"; return false; }
     P.prec = p->prec;
     P.nrep = n_rep;
@@ -641,6 +642,7 @@ void set_scalars(Dev &D, const hd_params *p) {
     D.half_skin2_f = (float)(D.half_skin2 * (1.0 - 1e-4));
     D.seed_lo = (uint32_t)p->seed;
     D.seed_hi = (uint32_t)(p->seed >> 32);
+    D.pair_x2 = p->pair_kernel == 1 ? 1 : 0;
 }
 
 hd_status check_device(hd_ctx *c) {
@@ -833,7 +835,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
             hx[a0 + sl] = make_dbl4(x[0], x[1], x[2], (double)d.type[i]);
             hxo[a0 + sl] = make_dbl4(xo[0], xo[1], xo[2], 0.0);
             hp[a0 + sl].p = make_int4(0, 0, 0, (int)d.type[i] | ((int)d.role[i] << 8));
-            hp[a0 + sl].d = make_float4(0.f, 0.f, 0.f, 0.f);
+            hp[a0 + sl].d = make_int4(0, 0, 0, 0);
             double v[3] = {0, 0, 0};
             if (d.vel && d.role[i] != 0)
                 for (int a = 0; a < 3; ++a) v[a] = d.vel[3 * i + a];

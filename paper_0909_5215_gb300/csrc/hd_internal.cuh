@@ -58,10 +58,12 @@ enum { MODE_CLOSE = 1, MODE_OPEN = 2, MODE_KIN = 4, MODE_NHC = 8, MODE_SCALE = 1
 enum { ROLE_FIXED = 0, ROLE_MOBILE = 1, ROLE_RIGID = 2 };
 
 // Per-atom record read by the pair sweep: fixed-point position (w = type |
-// role << 8) and, in the split form, r - r_O in FP32; one 32-byte sector.
+// role << 8) and, in the split form, r - r_O on the same fixed-point grid (w
+// unused); one 32-byte sector.  Differences of two atoms' r - r_O, which the
+// Hessian-vector term takes, are then exact integers.
 struct __align__(32) AtomRec {
     int4 p;
-    float4 d;
+    int4 d;
 };
 
 struct RepDev {
@@ -165,6 +167,7 @@ struct Dev {
     int nl_pow2, nl_grid;        // neighbour-row buffer (power of two >= maxnb), k_nlist CTAs
     int any_nhc;                 // some replica runs a Nose-Hoover chain: the update splits around it
     int any_eig;                 // some replica has the eigenvalue bias
+    int pair_x2;                 // split form: the packed FP32x2 pair sweep (tiles <= 128 atoms)
     dbl4 *eq, *ev, *ew, *eg;     // eigenvalue bias: Krylov bases, eigenvector, work vector, grad epsilon
     double *ealpha, *ebeta, *ey, *ecoef;  // tridiagonal (alpha, beta), its eigenvector, coefficients
     double *epart;               // per tile: sum of grad epsilon over rigid atoms (4 doubles)
@@ -246,6 +249,24 @@ __device__ __forceinline__ int fix_coord(const RepDev &R, int a, double x) {
 
 __device__ __forceinline__ int4 fix_pos(const RepDev &R, dbl4 x, int w) {
     return make_int4(fix_coord(R, 0, x.x), fix_coord(R, 1, x.y), fix_coord(R, 2, x.z), w);
+}
+
+// r - r_O on the pair sweep's fixed-point grid (no origin, no wrap).  The
+// grid's int32 range covers |r - r_O| < L / 2^(k+1) >= 4 (rc + skin); beyond
+// it (an atom that has left its basin by that much without a new r_O) the
+// value saturates and *far is set.
+__device__ __forceinline__ int fix_disp(const RepDev &R, int a, double d, bool &far) {
+    if (R.fx_scale[a] == 0.0) return 0;
+    const double q = rint(d * R.fx_scale[a]);
+    if (!(fabs(q) < 2147483647.0)) {
+        far = true;
+        return q > 0.0 ? 2147483647 : -2147483647;
+    }
+    return (int)q;
+}
+__device__ __forceinline__ int4 fix_dr(const RepDev &R, dbl4 x, dbl4 xo, bool &far) {
+    return make_int4(fix_disp(R, 0, x.x - xo.x, far), fix_disp(R, 1, x.y - xo.y, far),
+                     fix_disp(R, 2, x.z - xo.z, far), 0);
 }
 
 // Cell of an FP64 coordinate: exact integer map on periodic axes (the image

@@ -129,7 +129,11 @@ __global__ void k_init(Dev D, const int *draw_vel) {
     if (D.prec == HD_FP64)
         D.dr64[i] = make_dbl4(x.x - xo.x, x.y - xo.y, x.z - xo.z, 0.0);
     else
-        D.rec[i].d = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
+        {
+            bool far = false;
+            D.rec[i].d = fix_dr(R, x, xo, far);
+            if (far) set_err(D, HD_ERR_NUMERIC, i, r);
+        }
     if (draw_vel[r]) {
         double v0 = 0, v1 = 0, v2 = 0;
         if (role == ROLE_MOBILE) {
@@ -599,7 +603,25 @@ __device__ __forceinline__ float rcp_refined(float x) {
     return fmaf(y, fmaf(-x, y, 1.f), y);
 }
 
-template <bool Q, bool E>
+// Asynchronous 4-byte copies global -> shared (cp.async): each lane stages
+// its own atom's list entries, so a chunk needs no barrier, only the wait.
+__device__ __forceinline__ void cp_async4(int *dst, const int *src) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// List entries a lane stages ahead per chunk, double-buffered: a warp keeps
+// 2 x NBC x 128 B of its column-major list rows in shared memory, the next
+// chunk in flight while the current one is used.
+constexpr int NBC = 16;
+__host__ __device__ constexpr size_t pair_smem_bytes_for(int block) {
+    return (size_t)(block / 32) * 2 * NBC * 32 * sizeof(int);
+}
+
+template <bool Q, bool E, bool X2 = false>
 __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const int r = D.tile_rep[t];
     if (Q && D.st[r].q_done) return;
@@ -609,8 +631,9 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const AtomRec ai = D.rec[i];
     const int4 pi = ai.p;
     const int ti = pi.w & 1;
-    const float4 dri = Q ? make_float4(0.f, 0.f, 0.f, 0.f) : ai.d;
     const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
+    const int4 dfi = Q ? make_int4(0, 0, 0, 0) : ai.d;                 // r - r_O, fixed point
+    const float4 dri = make_float4((float)dfi.x * lx, (float)dfi.y * ly, (float)dfi.z * lz, 0.f);
     const float e0 = R.epsf[ti][0], e1 = R.epsf[ti][1];
     const float a0 = R.eps24f[ti][0], a1 = R.eps24f[ti][1];
     const float b0 = R.eps96f[ti][0], b1 = R.eps96f[ti][1];
@@ -623,11 +646,27 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const int nn = act ? D.nnb[i] : 0;
     const int *nb = D.nbr + i;
     const size_t stride = (size_t)D.natom;
-    // software pipeline: while neighbour k is used, the record of k + 1 and the
-    // index of k + 2 are in flight, so no iteration waits on an index load.
-    // plain loads: in the persistent launch the list is rewritten between steps
-    AtomRec an = D.rec[nn > 0 ? nb[0] : i];
-    int jn = nn > 1 ? nb[stride] : i;
+    // The list streams from HBM: each lane stages its row NBC entries at a
+    // time through shared memory by cp.async, the next chunk in flight while
+    // the current one is used; the record of the next entry is loaded while
+    // the current one is used.
+    extern __shared__ __align__(16) int pair_smem[];
+    const int lane = threadIdx.x & 31;
+    int(*sbuf)[NBC][32] = reinterpret_cast<int(*)[NBC][32]>(pair_smem) + 2 * (threadIdx.x >> 5);
+    int nmax = nn;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    const int nch = (nmax + NBC - 1) / NBC;
+    auto stage = [&](int c) {
+        int(*b)[32] = sbuf[c & 1];
+#pragma unroll
+        for (int u = 0; u < NBC; ++u) {
+            const int k = c * NBC + u;
+            if (k < nn) cp_async4(&b[u][lane], nb + (size_t)k * stride);
+        }
+        cp_async_commit();
+    };
+    if (nch > 0) stage(0);
     // one pair's contribution.  Cancellation-free LJ form: 2 s^6 - 1 = w(tt)
     // with tt = (r_0^2 - r^2) / r^2.  Where |tt| < 1/4 (around the minimum,
     // where w is small and the FP32 r^2 would cost it its relative accuracy)
@@ -658,7 +697,9 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
         fz = fmaf(fr, dz, fz);
         if (E) e = fmaf(0.5f, fmaf(4.f * (tj ? e1 : e0) * s6, s6 - 1.f, -(tj ? h1 : h0)), e);
         if (!Q) {
-            const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
+            const float ux = (float)(int)((unsigned)dfi.x - (unsigned)aj.d.x) * lx;
+            const float uy = (float)(int)((unsigned)dfi.y - (unsigned)aj.d.y) * ly;
+            const float uz = (float)(int)((unsigned)dfi.z - (unsigned)aj.d.z) * lz;
             const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
             const float B = (tj ? b1 : b0) * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
             hx = fmaf(-fr, ux, fmaf(B, dx, hx));
@@ -667,18 +708,131 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
         }
     };
     bool band = false;
-    for (int k = 0; k < nn; ++k) {
-        const AtomRec aj = an;
-        if (k + 1 < nn) an = D.rec[jn];
-        if (k + 2 < nn) jn = nb[(size_t)(k + 2) * stride];
-        const int4 pj = aj.p;
-        const int ix = (int)((unsigned)pi.x - (unsigned)pj.x);
-        const int iy = (int)((unsigned)pi.y - (unsigned)pj.y);
-        const int iz = (int)((unsigned)pi.z - (unsigned)pj.z);
-        const float dx = (float)ix * lx, dy = (float)iy * ly, dz = (float)iz * lz;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < D.rc2_lo_f) term(aj, ix, iy, iz, dx, dy, dz, r2);
-        else band |= r2 < D.rc2_hi_f;
+    if (!X2) {
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) {
+                stage(c + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            const int(*b)[32] = sbuf[c & 1];
+            const int kend = min(NBC, nn - c * NBC);
+            AtomRec an = kend > 0 ? D.rec[b[0][lane]] : ai;
+            for (int u = 0; u < kend; ++u) {
+                const AtomRec aj = an;
+                if (u + 1 < kend) an = D.rec[b[u + 1][lane]];
+                const int4 pj = aj.p;
+                const int ix = (int)((unsigned)pi.x - (unsigned)pj.x);
+                const int iy = (int)((unsigned)pi.y - (unsigned)pj.y);
+                const int iz = (int)((unsigned)pi.z - (unsigned)pj.z);
+                const float dx = (float)ix * lx, dy = (float)iy * ly, dz = (float)iz * lz;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < D.rc2_lo_f) term(aj, ix, iy, iz, dx, dy, dz, r2);
+                else band |= r2 < D.rc2_hi_f;
+            }
+        }
+    } else {
+        // Two list entries per iteration in packed FP32x2 arithmetic (one
+        // instruction for both halves), with the same operations per entry as
+        // term(); an entry outside the cutoff contributes through a select to
+        // zero.  Records of the next two entries and the indices of the two
+        // after them are in flight while the current two are used.
+        const float2 one2 = make_float2(1.f, 1.f), mone2 = make_float2(-1.f, -1.f), half2 = make_float2(0.5f, 0.5f);
+        const float2 three2 = make_float2(3.f, 3.f), seven2 = make_float2(7.f, 7.f), mtwo2 = make_float2(-2.f, -2.f);
+        const float2 corr2 = make_float2(r2corr, r2corr);
+        float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx, Hx = Fx, Hy = Fx, Hz = Fx, Ee = Fx;
+        for (int c = 0; c < nch; ++c) {
+          if (c + 1 < nch) {
+              stage(c + 1);
+              cp_async_wait<1>();
+          } else {
+              cp_async_wait<0>();
+          }
+          const int(*b)[32] = sbuf[c & 1];
+          const int kend = min(NBC, nn - c * NBC);
+          AtomRec na = kend > 0 ? D.rec[b[0][lane]] : ai, nbr2 = kend > 1 ? D.rec[b[1][lane]] : ai;
+          for (int u = 0; u < kend; u += 2) {
+            const AtomRec A = na, B = nbr2;
+            const bool vb = u + 1 < kend;
+            if (u + 2 < kend) na = D.rec[b[u + 2][lane]];
+            if (u + 3 < kend) nbr2 = D.rec[b[u + 3][lane]];
+            const int ixa = (int)((unsigned)pi.x - (unsigned)A.p.x), ixb = (int)((unsigned)pi.x - (unsigned)B.p.x);
+            const int iya = (int)((unsigned)pi.y - (unsigned)A.p.y), iyb = (int)((unsigned)pi.y - (unsigned)B.p.y);
+            const int iza = (int)((unsigned)pi.z - (unsigned)A.p.z), izb = (int)((unsigned)pi.z - (unsigned)B.p.z);
+            const float2 dx = __fmul2_rn(make_float2((float)ixa, (float)ixb), make_float2(lx, lx));
+            const float2 dy = __fmul2_rn(make_float2((float)iya, (float)iyb), make_float2(ly, ly));
+            const float2 dz = __fmul2_rn(make_float2((float)iza, (float)izb), make_float2(lz, lz));
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const bool ina = r2.x < D.rc2_lo_f, inb = vb && r2.y < D.rc2_lo_f;
+            band |= (!ina && r2.x < D.rc2_hi_f) || (vb && !inb && r2.y < D.rc2_hi_f);
+            if (!(ina || inb)) continue;
+            const int ta = A.p.w & 1, tb = B.p.w & 1;
+            const float2 r0h = make_float2(ta ? q1h : q0h, tb ? q1h : q0h);
+            const float2 r0l = make_float2(ta ? q1l : q0l, tb ? q1l : q0l);
+            const float2 r2c = __ffma2_rn(r2, corr2, r2);
+            float2 ir2 = make_float2(rcp_approx(r2c.x), rcp_approx(r2c.y));
+            ir2 = __ffma2_rn(ir2, __ffma2_rn(r2c, __fmul2_rn(ir2, mone2), one2), ir2);
+            float2 tt = __fmul2_rn(__fadd2_rn(__ffma2_rn(r2c, mone2, r0h), r0l), ir2);
+            if (exact && ina && fabsf(tt.x) < 0.25f) {
+                float h, l;
+                r2_split(R, ixa, iya, iza, h, l);
+                ir2.x = rcp_refined(h);
+                tt.x = ((r0h.x - h) + (r0l.x - l)) * ir2.x;
+            }
+            if (exact && inb && fabsf(tt.y) < 0.25f) {
+                float h, l;
+                r2_split(R, ixb, iyb, izb, h, l);
+                ir2.y = rcp_refined(h);
+                tt.y = ((r0h.y - h) + (r0l.y - l)) * ir2.y;
+            }
+            const float2 u1 = __fadd2_rn(one2, tt);
+            const float2 s6 = __fmul2_rn(__fmul2_rn(half2, u1), __fmul2_rn(u1, u1));
+            const float2 w = __fmul2_rn(tt, __ffma2_rn(tt, __fadd2_rn(tt, three2), three2));      // 2 s^6 - 1
+            float2 fr = __fmul2_rn(__fmul2_rn(make_float2(ta ? a1 : a0, tb ? a1 : a0), ir2), __fmul2_rn(s6, w));
+            fr.x = ina ? fr.x : 0.f;
+            fr.y = inb ? fr.y : 0.f;
+            Fx = __ffma2_rn(fr, dx, Fx);
+            Fy = __ffma2_rn(fr, dy, Fy);
+            Fz = __ffma2_rn(fr, dz, Fz);
+            if (E) {
+                float2 ee = __ffma2_rn(__fmul2_rn(make_float2(4.f * (ta ? e1 : e0), 4.f * (tb ? e1 : e0)), s6),
+                                       __fadd2_rn(s6, mone2), make_float2(-(ta ? h1 : h0), -(tb ? h1 : h0)));
+                ee.x = ina ? ee.x : 0.f;
+                ee.y = inb ? ee.y : 0.f;
+                Ee = __ffma2_rn(half2, ee, Ee);
+            }
+            if (!Q) {
+                const float2 ux = __fmul2_rn(make_float2((float)(int)((unsigned)dfi.x - (unsigned)A.d.x),
+                                                         (float)(int)((unsigned)dfi.x - (unsigned)B.d.x)),
+                                             make_float2(lx, lx));
+                const float2 uy = __fmul2_rn(make_float2((float)(int)((unsigned)dfi.y - (unsigned)A.d.y),
+                                                         (float)(int)((unsigned)dfi.y - (unsigned)B.d.y)),
+                                             make_float2(ly, ly));
+                const float2 uz = __fmul2_rn(make_float2((float)(int)((unsigned)dfi.z - (unsigned)A.d.z),
+                                                         (float)(int)((unsigned)dfi.z - (unsigned)B.d.z)),
+                                             make_float2(lz, lz));
+                const float2 rdu = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
+                float2 Bc = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(ta ? b1 : b0, tb ? b1 : b0), ir2), ir2),
+                                       __fmul2_rn(__fmul2_rn(s6, __ffma2_rn(seven2, s6, mtwo2)), rdu));
+                Bc.x = ina ? Bc.x : 0.f;
+                Bc.y = inb ? Bc.y : 0.f;
+                const float2 nfr = __fmul2_rn(fr, mone2);
+                Hx = __ffma2_rn(nfr, ux, __ffma2_rn(Bc, dx, Hx));
+                Hy = __ffma2_rn(nfr, uy, __ffma2_rn(Bc, dy, Hy));
+                Hz = __ffma2_rn(nfr, uz, __ffma2_rn(Bc, dz, Hz));
+            }
+          }
+        }
+        fx += Fx.x + Fx.y;
+        fy += Fy.x + Fy.y;
+        fz += Fz.x + Fz.y;
+        if (E) e += Ee.x + Ee.y;
+        if (!Q) {
+            hx += Hx.x + Hx.y;
+            hy += Hy.x + Hy.y;
+            hz += Hz.x + Hz.y;
+        }
     }
     // Rare: pairs in a thin band around rc are cut by the oracle's FP64 test
     // (same operations), so no pair is cut at a different step than in FP64.
@@ -719,7 +873,9 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
             fz = fmaf(-A, dz, fz);
             if (E) e = fmaf(0.25f * R.kbondf * db, db, e);
             if (!Q) {
-                const float ux = dri.x - aj.d.x, uy = dri.y - aj.d.y, uz = dri.z - aj.d.z;
+                const float ux = (float)(int)((unsigned)dfi.x - (unsigned)aj.d.x) * lx;
+                const float uy = (float)(int)((unsigned)dfi.y - (unsigned)aj.d.y) * ly;
+                const float uz = (float)(int)((unsigned)dfi.z - (unsigned)aj.d.z) * lz;
                 const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
                 const float B = (R.kbondf - A) * ir * ir * rdu;
                 hx = fmaf(A, ux, fmaf(B, dx, hx));
@@ -793,6 +949,9 @@ template <bool Q, bool E>
 __global__ void __launch_bounds__(256) k_pair64(Dev D) { dev_pair64<Q, E>(D, blockIdx.x); }
 template <bool Q, bool E>
 __global__ void __launch_bounds__(256, 4) k_pair32(Dev D) { dev_pair32<Q, E>(D, blockIdx.x); }
+// the packed FP32x2 variant: more registers a thread, fewer warps resident
+template <bool Q, bool E>
+__global__ void __launch_bounds__(128, 5) k_pair32x2(Dev D) { dev_pair32<Q, E, true>(D, blockIdx.x); }
 
 // ---------------------------------------------------------------- per-replica scalars
 // Gathers the replica's tile sums (warp q sums slot q over the tiles in a
@@ -1123,7 +1282,9 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
         dbl4 v = D.v64[i];
         dbl4 x = D.x[i];
         if (role == ROLE_MOBILE) {
-            const float4 F = D.f32[i], H = D.h32[i], dr = ai.d;
+            const float4 F = D.f32[i], H = D.h32[i];
+            const float4 dr = make_float4((float)ai.d.x * R.fx_lsb[0], (float)ai.d.y * R.fx_lsb[1],
+                                          (float)ai.d.z * R.fx_lsb[2], 0.f);
             const float ca = (float)C.ca, cb = (float)C.cb;
             double Fx = (double)fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
             double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
@@ -1191,7 +1352,11 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
         if (mode & MODE_OPEN) {
             D.x[i] = x;
             const dbl4 xo = D.xo[i];
-            D.rec[i].d = make_float4((float)(x.x - xo.x), (float)(x.y - xo.y), (float)(x.z - xo.z), 0.f);
+            {
+                bool far = false;
+                D.rec[i].d = fix_dr(R, x, xo, far);
+                if (far) set_err(D, HD_ERR_NUMERIC, i, r);
+            }
             post_move(D, R, r, i, x, p);
         }
     }
@@ -1414,7 +1579,11 @@ __global__ void k_adopt(Dev Q, Dev M, const int *adopt) {
     M.xo[i] = make_dbl4(q.x, q.y, q.z, 0.0);
     const dbl4 x = M.x[i];
     if (M.prec == HD_FP64) M.dr64[i] = make_dbl4(x.x - q.x, x.y - q.y, x.z - q.z, 0.0);
-    else M.rec[i].d = make_float4((float)(x.x - q.x), (float)(x.y - q.y), (float)(x.z - q.z), 0.f);
+    else {
+        bool far = false;
+        M.rec[i].d = fix_dr(M.rep[r], x, make_dbl4(q.x, q.y, q.z, 0.0), far);
+        if (far) set_err(M, HD_ERR_NUMERIC, i, r);
+    }
 }
 
 // ---------------------------------------------------------------- persistent driver
@@ -1581,13 +1750,18 @@ size_t nl_smem_bytes(const Dev &D) {
     const size_t cmax = 27 * (size_t)D.cell_cap;
     return cmax * (sizeof(int4) + sizeof(int)) + cmax * 4;
 }
+// the persistent kernel runs the list build and the pair sweep in one launch
+static size_t persist_smem_bytes(const Dev &D) {
+    const size_t a = nl_smem_bytes(D), b = pair_smem_bytes_for(D.block);
+    return a > b ? a : b;
+}
 cudaError_t nl_configure(const Dev &D) {
-    const int bytes = (int)nl_smem_bytes(D);
+    const int bytes = (int)nl_smem_bytes(D), pbytes = (int)persist_smem_bytes(D);
     cudaError_t e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_persist<HD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(k_persist<HD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_persist<HD_FP32_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_persist<HD_FP32_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
 }
 
 void launch_init(const Dev &D, const int *draw_vel, cudaStream_t s) {
@@ -1609,10 +1783,16 @@ void launch_pair(const Dev &D, bool quench, bool energy, cudaStream_t s) {
         if (quench) k_pair64<true, false><<<D.ntile, nthr(D), 0, s>>>(D);
         else if (energy) k_pair64<false, true><<<D.ntile, nthr(D), 0, s>>>(D);
         else k_pair64<false, false><<<D.ntile, nthr(D), 0, s>>>(D);
+    } else if (D.pair_x2 && D.block <= 128) {
+        const size_t sm = pair_smem_bytes_for(D.block);
+        if (quench) k_pair32x2<true, false><<<D.ntile, nthr(D), sm, s>>>(D);
+        else if (energy) k_pair32x2<false, true><<<D.ntile, nthr(D), sm, s>>>(D);
+        else k_pair32x2<false, false><<<D.ntile, nthr(D), sm, s>>>(D);
     } else {
-        if (quench) k_pair32<true, false><<<D.ntile, nthr(D), 0, s>>>(D);
-        else if (energy) k_pair32<false, true><<<D.ntile, nthr(D), 0, s>>>(D);
-        else k_pair32<false, false><<<D.ntile, nthr(D), 0, s>>>(D);
+        const size_t sm = pair_smem_bytes_for(D.block);
+        if (quench) k_pair32<true, false><<<D.ntile, nthr(D), sm, s>>>(D);
+        else if (energy) k_pair32<false, true><<<D.ntile, nthr(D), sm, s>>>(D);
+        else k_pair32<false, false><<<D.ntile, nthr(D), sm, s>>>(D);
     }
 }
 void launch_scalar(const Dev &D, int mode, cudaStream_t s) {
@@ -1634,7 +1814,7 @@ void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s) {
 void launch_qdisp(const Dev &Q, cudaStream_t s) { k_qdisp<<<Q.ntile, nthr(Q), 0, s>>>(Q); }
 int persist_blocks_per_sm(const Dev &D) {
     int nb = 0;
-    const size_t sm = nl_smem_bytes(D);
+    const size_t sm = persist_smem_bytes(D);
     if (D.prec == HD_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP64>, D.block, sm);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persist<HD_FP32_SPLIT>, D.block, sm);
     return nb;
@@ -1647,7 +1827,7 @@ cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(D.block);
-    cfg.dynamicSmemBytes = nl_smem_bytes(D);
+    cfg.dynamicSmemBytes = persist_smem_bytes(D);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

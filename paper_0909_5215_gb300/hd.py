@@ -59,7 +59,7 @@ class hd_replica_desc(C.Structure):
 class hd_params(C.Structure):
     _fields_ = [("prec", C.c_int), ("bias_on", C.c_int), ("driver", C.c_int), ("block", C.c_int),
                 ("dt", C.c_double), ("rc", C.c_double), ("skin", C.c_double), ("seed", C.c_uint64),
-                ("maxnb", C.c_int), ("cell_cap", C.c_int)]
+                ("maxnb", C.c_int), ("cell_cap", C.c_int), ("pair_kernel", C.c_int), ("pad_", C.c_int)]
 
 
 SYMBOLS = ["hd_workspace_bytes", "hd_create", "hd_set_slider", "hd_set_bias", "hd_step", "hd_quench",
@@ -175,10 +175,10 @@ def hd_last_error(ctx):
 
 
 # ---------------------------------------------------------------- convenience
-def make_params(params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, prec=None):
+def make_params(params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, prec=None, pair_kernel=0):
     return hd_params(int(params.prec if prec is None else prec), int(params.bias_on), int(driver), int(block),
                      float(params.dt), float(params.rc), float(params.skin), int(params.seed), int(maxnb),
-                     int(cell_cap))
+                     int(cell_cap), int(pair_kernel), 0)
 
 
 def make_descs(reps):
@@ -239,14 +239,14 @@ class Batch:
     """One library context over a batch of replicas on one GPU."""
 
     def __init__(self, reps, params, driver=HD_DRIVER_AUTO, block=0, maxnb=0, cell_cap=0, prec=None,
-                 device="cuda:0", stream=None):
+                 device="cuda:0", stream=None, pair_kernel=0):
         import torch
         self.reps = reps
         self.n_rep = len(reps)
         self.ns = [r.n for r in reps]
         self.torch = torch
         self.device = torch.device(device)
-        self.params = make_params(params, driver, block, maxnb, cell_cap, prec)
+        self.params = make_params(params, driver, block, maxnb, cell_cap, prec, pair_kernel)
         self.prec = self.params.prec
         descs, keep = make_descs(reps)
         nb = hd_workspace_bytes(descs, len(reps), self.params)

@@ -9,18 +9,21 @@ def test_choose_and_cache(tmp_path):
     p = M.Params(prec=1)
     calls = []
 
-    def fake(rs, params, driver, block, steps, warm):
-        calls.append((driver, block))
-        return {(hd.HD_DRIVER_KERNELS, 128): 2.0, (hd.HD_DRIVER_PERSISTENT, 128): 1.5}.get((driver, block), 3.0)
+    def fake(rs, params, driver, block, steps, warm, pair_kernel=0):
+        calls.append((driver, block, pair_kernel))
+        return {(hd.HD_DRIVER_KERNELS, 128, 1): 2.0, (hd.HD_DRIVER_PERSISTENT, 128, 0): 1.5}.get(
+            (driver, block, pair_kernel), 3.0)
 
     cache = str(tmp_path / "tune.json")
-    drv, blk, ms = autotune.tune(reps, p, cache=cache, timer=fake)
-    assert (drv, blk) == (hd.HD_DRIVER_PERSISTENT, 128)
+    drv, blk, pk, ms = autotune.tune(reps, p, cache=cache, timer=fake)
+    assert (drv, blk, pk) == (hd.HD_DRIVER_PERSISTENT, 128, 0)
     assert len(calls) == len(autotune.CANDIDATES)
-    drv2, blk2, _ = autotune.tune(reps, p, cache=cache, timer=fake)     # cached: no new timings
-    assert (drv2, blk2) == (drv, blk) and len(calls) == len(autotune.CANDIDATES)
+    drv2, blk2, pk2, _ = autotune.tune(reps, p, cache=cache, timer=fake)     # cached: no new timings
+    assert (drv2, blk2, pk2) == (drv, blk, pk) and len(calls) == len(autotune.CANDIDATES)
     assert autotune.signature(reps, p) != autotune.signature(reps[:1], p)
-    assert autotune.choose({(1, 64): None, (1, 128): None}) == (hd.HD_DRIVER_KERNELS, 128)
+    assert autotune.choose({(1, 64, 0): None, (1, 128, 0): None}) == (hd.HD_DRIVER_KERNELS, 128, 0)
+    # the FP64 form has no packed pair sweep to try
+    assert all(c[2] == 0 for c in autotune.candidates(M.Params(prec=0)))
 
 
 def test_rebuilt_library_or_corrupt_cache_is_tuned_afresh(tmp_path, monkeypatch):
@@ -30,13 +33,13 @@ def test_rebuilt_library_or_corrupt_cache_is_tuned_afresh(tmp_path, monkeypatch)
     p = M.Params(prec=1)
     calls = []
 
-    def fake(rs, params, driver, block, steps, warm):
-        calls.append((driver, block))
-        return 1.0 if (driver, block) == (hd.HD_DRIVER_KERNELS, 64) else 2.0
+    def fake(rs, params, driver, block, steps, warm, pair_kernel=0):
+        calls.append((driver, block, pair_kernel))
+        return 1.0 if (driver, block, pair_kernel) == (hd.HD_DRIVER_KERNELS, 64, 1) else 2.0
 
     cache = str(tmp_path / "sub" / "tune.json")
     monkeypatch.setattr(autotune, "build_identity", lambda: "lib1:1|GPU A")
-    assert autotune.tune(reps, p, cache=cache, timer=fake)[:2] == (hd.HD_DRIVER_KERNELS, 64)
+    assert autotune.tune(reps, p, cache=cache, timer=fake)[:3] == (hd.HD_DRIVER_KERNELS, 64, 1)
     n = len(calls)
     autotune.tune(reps, p, cache=cache, timer=fake)
     assert len(calls) == n                                  # same build: cached
@@ -48,4 +51,4 @@ def test_rebuilt_library_or_corrupt_cache_is_tuned_afresh(tmp_path, monkeypatch)
     autotune.tune(reps, p, cache=cache, timer=fake)
     assert len(calls) == 3 * n                              # unreadable cache: timed again
     # every candidate failing falls back to the per-phase kernels
-    assert autotune.choose({c: None for c in autotune.CANDIDATES}) == (hd.HD_DRIVER_KERNELS, 128)
+    assert autotune.choose({c: None for c in autotune.CANDIDATES}) == (hd.HD_DRIVER_KERNELS, 128, 0)

@@ -398,3 +398,26 @@ def test_quench_sd_3d_workload_model(hd, oracle_mod, workload_states, prec):
     b.quench(method=0, ftol=1e-12, max_iter=50, step_size=0.002, theta=0.0, adopt=2)
     assert np.array_equal(b.ref(0), st.pos_ref)
     b.close()
+
+
+def test_packed_pair_sweep_matches_oracle(hd, oracle_mod, states):
+    """The packed FP32x2 pair sweep (two list entries per thread per
+    instruction) holds the split form's bounds: forces, H.(r - r_O) and
+    energies within 1e-5 RMS, and 100 biased steps within the trajectory
+    bounds of the scalar sweep."""
+    reps = [states["2d"], states["3d"], states["3d_big"]]
+    p = _params(prec=1, bias_on=1)
+    b = hd.Batch(reps, p, pair_kernel=1)
+    ors = [oracle_mod.OracleReplica(r, p) for r in reps]
+    for k, o in enumerate(ors):
+        assert rms_rel(b.forces(k), o.f_lj) <= 1e-5
+        assert rms_rel(b.hdr(k), o.hdr) <= 1e-5
+        assert rms_rel(b.energies(k), o.e_atom) <= 1e-5
+        assert b.obs(k)["sigma"] == pytest.approx(o.s.sigma, rel=1e-6)
+    b.step(100)
+    for k, o in enumerate(ors):
+        o.run(100)
+        ob = b.obs(k)
+        assert np.abs(b.positions(k) - o.x).max() < 1e-4
+        assert abs(ob["dV"] - o.s.dV) <= dv_bound(o, 1) * 30
+    b.close()
