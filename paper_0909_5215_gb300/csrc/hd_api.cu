@@ -258,6 +258,8 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
                 R.r0sq_lo[a][b] = (float)(r0sq - (double)R.r0sq_hi[a][b]);
                 R.eps24f[a][b] = (float)(24.0 * eps);
                 R.eps96f[a][b] = (float)(96.0 * eps);
+                R.eps24l[a][b] = (float)(24.0 * eps - (double)R.eps24f[a][b]);
+                R.eps96l[a][b] = (float)(96.0 * eps - (double)R.eps96f[a][b]);
                 // the pair sweep takes the exact r^2 where |r_0^2 - r^2| < r^2 / 4,
                 // i.e. r^2 < (4/3) r_0^2; class A of the list holds the pairs within
                 // that radius plus 0.1 sigma at build time
@@ -308,6 +310,8 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
             R.shiftf[1][1] = 0.f;
             R.eps24f[1][1] = 0.f;
             R.eps96f[1][1] = 0.f;
+            R.eps24l[1][1] = 0.f;
+            R.eps96l[1][1] = 0.f;
         }
         P.rep[r] = R;
         for (int k = 0; k < R.ntile; ++k) {

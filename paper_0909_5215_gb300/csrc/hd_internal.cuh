@@ -93,7 +93,8 @@ struct RepDev {
     float lsb_rel[3];            // (unit - fl32(unit)) / fl32(unit) per axis
     float pad2;
     float r0sq_hi[2][2], r0sq_lo[2][2];  // 2^(1/3) sigma_ab^2 (LJ minimum, squared) as hi + lo
-    float eps24f[2][2], eps96f[2][2];    // 24 eps_ab, 96 eps_ab
+    float eps24f[2][2], eps96f[2][2];    // 24 eps_ab, 96 eps_ab (FP32 rounding) ...
+    float eps24l[2][2], eps96l[2][2];    // ... and the remainders (hi + lo = the FP64 value)
     float rA2f;                  // list class A (first shell): FP32 r^2 below this at build time
     float kbondf;                // Eq. 12 bonds: stiffness (FP32)
     double kbond, rbond;         // Eq. 12 bonds: stiffness, rest length

@@ -635,8 +635,10 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
     const int4 dfi = Q ? make_int4(0, 0, 0, 0) : ai.d;                 // r - r_O, fixed point
     const float4 dri = make_float4((float)dfi.x * lx, (float)dfi.y * ly, (float)dfi.z * lz, 0.f);
     const float e0 = R.epsf[ti][0], e1 = R.epsf[ti][1];
-    const float a0 = R.eps24f[ti][0], a1 = R.eps24f[ti][1];
-    const float b0 = R.eps96f[ti][0], b1 = R.eps96f[ti][1];
+    // 24 eps and 96 eps as FP32 hi + lo: an eps such as 0.2 is not an FP32
+    // number, and its rounding would scale every such pair force alike
+    const float a0 = R.eps24f[ti][0], a1 = R.eps24f[ti][1], al0 = R.eps24l[ti][0], al1 = R.eps24l[ti][1];
+    const float b0 = R.eps96f[ti][0], b1 = R.eps96f[ti][1], bl0 = R.eps96l[ti][0], bl1 = R.eps96l[ti][1];
     const float h0 = R.shiftf[ti][0], h1 = R.shiftf[ti][1];
     const float q0h = R.r0sq_hi[ti][0], q1h = R.r0sq_hi[ti][1];
     const float q0l = R.r0sq_lo[ti][0], q1l = R.r0sq_lo[ti][1];
@@ -691,7 +693,8 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
         const float u = 1.f + tt;
         const float s6 = 0.5f * u * u * u;
         const float w = tt * fmaf(tt, tt + 3.f, 3.f);          // 2 s^6 - 1
-        const float fr = (tj ? a1 : a0) * ir2 * s6 * w;
+        const float pf = ir2 * s6 * w;
+        const float fr = fmaf(pf, tj ? al1 : al0, pf * (tj ? a1 : a0));
         fx = fmaf(fr, dx, fx);
         fy = fmaf(fr, dy, fy);
         fz = fmaf(fr, dz, fz);
@@ -701,7 +704,8 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
             const float uy = (float)(int)((unsigned)dfi.y - (unsigned)aj.d.y) * ly;
             const float uz = (float)(int)((unsigned)dfi.z - (unsigned)aj.d.z) * lz;
             const float rdu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-            const float B = (tj ? b1 : b0) * ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
+            const float pb = ir2 * ir2 * s6 * fmaf(7.f, s6, -2.f) * rdu;
+            const float B = fmaf(pb, tj ? bl1 : bl0, pb * (tj ? b1 : b0));
             hx = fmaf(-fr, ux, fmaf(B, dx, hx));
             hy = fmaf(-fr, uy, fmaf(B, dy, hy));
             hz = fmaf(-fr, uz, fmaf(B, dz, hz));
@@ -789,7 +793,9 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
             const float2 u1 = __fadd2_rn(one2, tt);
             const float2 s6 = __fmul2_rn(__fmul2_rn(half2, u1), __fmul2_rn(u1, u1));
             const float2 w = __fmul2_rn(tt, __ffma2_rn(tt, __fadd2_rn(tt, three2), three2));      // 2 s^6 - 1
-            float2 fr = __fmul2_rn(__fmul2_rn(make_float2(ta ? a1 : a0, tb ? a1 : a0), ir2), __fmul2_rn(s6, w));
+            const float2 pf = __fmul2_rn(ir2, __fmul2_rn(s6, w));
+            float2 fr = __ffma2_rn(pf, make_float2(ta ? al1 : al0, tb ? al1 : al0),
+                                   __fmul2_rn(pf, make_float2(ta ? a1 : a0, tb ? a1 : a0)));
             fr.x = ina ? fr.x : 0.f;
             fr.y = inb ? fr.y : 0.f;
             Fx = __ffma2_rn(fr, dx, Fx);
@@ -813,8 +819,10 @@ __device__ __forceinline__ void dev_pair32(const Dev &D, int t) {
                                                          (float)(int)((unsigned)dfi.z - (unsigned)B.d.z)),
                                              make_float2(lz, lz));
                 const float2 rdu = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
-                float2 Bc = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(ta ? b1 : b0, tb ? b1 : b0), ir2), ir2),
-                                       __fmul2_rn(__fmul2_rn(s6, __ffma2_rn(seven2, s6, mtwo2)), rdu));
+                const float2 pb = __fmul2_rn(__fmul2_rn(ir2, ir2),
+                                             __fmul2_rn(__fmul2_rn(s6, __ffma2_rn(seven2, s6, mtwo2)), rdu));
+                float2 Bc = __ffma2_rn(pb, make_float2(ta ? bl1 : bl0, tb ? bl1 : bl0),
+                                       __fmul2_rn(pb, make_float2(ta ? b1 : b0, tb ? b1 : b0)));
                 Bc.x = ina ? Bc.x : 0.f;
                 Bc.y = inb ? Bc.y : 0.f;
                 const float2 nfr = __fmul2_rn(fr, mone2);
