@@ -39,7 +39,7 @@ struct Plan {
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
     size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff, o_rbaoff, o_rblist, o_rbmeta;
     size_t o_ctarep, o_pgfirst, o_pgcount, o_boff, o_bj;
-    size_t o_eq, o_ev, o_ew, o_eg, o_ealpha, o_ebeta, o_ey, o_ecoef, o_epart;
+    size_t o_eq, o_ev, o_ew, o_eg, o_ealpha, o_ebeta, o_ey, o_ecoef, o_epart, o_po;
     long long eig_q = 0, eig_t = 0;     // dbl4 entries of all Krylov bases, doubles of all tridiagonals
     bool any_eig = false;
 };
@@ -365,7 +365,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_x = take(cur, N * sizeof(dbl4));
     P.o_xo = take(cur, N * sizeof(dbl4));
     P.o_xq = take(cur, N * sizeof(dbl4));
-    P.o_v = take(cur, N * sizeof(dbl4));     // velocities are FP64 in both forms
+    P.o_v = take(cur, N * sizeof(dbl4));     // velocities: FP64 (FP64 form) or FP32 (split form)
     P.o_vq = take(cur, N * v4);
     P.o_f = take(cur, N * v4);
     P.o_fq = take(cur, N * v4);
@@ -395,6 +395,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_ctarep = take(cur, T * 4);       // at most one CTA per tile
     P.o_pgfirst = take(cur, R * 4);
     P.o_pgcount = take(cur, R * 4);
+    P.o_po = take(cur, (P.prec == HD_FP64 ? 1 : N) * 16);   // split form: fixed-point image of r_O
     P.o_boff = take(cur, (N + 1) * 4);
     P.o_bj = take(cur, std::max<size_t>(1, P.bond_j.size()) * 4);
     {
@@ -560,6 +561,8 @@ void fill_dev(hd_ctx *c) {
     D.x = at<dbl4>(b, P.o_x);
     D.xo = at<dbl4>(b, P.o_xo);
     D.v64 = at<dbl4>(b, P.o_v);
+    D.vf = at<float4>(b, P.o_v);          // the same block: FP64 form dbl4, split form float4
+    D.po = at<int4>(b, P.o_po);
     if (P.prec == HD_FP64) {
         D.f64 = at<dbl4>(b, P.o_f);
         D.h64 = at<dbl4>(b, P.o_h);
@@ -844,7 +847,10 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
             if (d.vel && d.role[i] != 0)
                 for (int a = 0; a < 3; ++a) v[a] = d.vel[3 * i + a];
             if (d.dim == 2) v[2] = 0.0;
-            reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
+            if (P.prec == HD_FP64)
+                reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
+            else   // split form: FP32 velocities
+                reinterpret_cast<float4 *>(hv.data())[a0 + sl] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
         }
     }
     if (upload_reps(c) != HD_OK) return c->status;
@@ -1149,7 +1155,7 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         return vec3(c->Q.x, true, -1);
     case HD_FIELD_VEL:
         if (!need(n * 24)) break;
-        return vec3(c->ws + P.o_v, true, -1);
+        return vec3(c->ws + P.o_v, f64, -1);
     case HD_FIELD_FORCE:
         if (!need(n * 24)) break;
         return vec3(c->ws + P.o_f, f64, -1);

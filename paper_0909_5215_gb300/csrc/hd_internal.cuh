@@ -7,11 +7,13 @@
 //     x      dbl4  FP64 position, w = LJ type           (never wrapped)
 //     xo     dbl4  basin minimum r_O
 //     v      dbl4 (FP64 form) | float4 (split form)    velocity
+//     po     int4 (split form)  fixed-point image of r_O
 //     f      dbl4 | float4   LJ force, w = per-atom energy (half of each pair)
 //     h      dbl4 | float4   H.(r - r_O), spring term included
 //     dr     dbl4 | float4   r - r_O
-//     rec    AtomRec  32-bit fixed-point position (w = type | role << 8) and
-//                     FP32 r - r_O of the split form, 32 bytes
+//     rec    AtomRec  32-bit fixed-point position (w = type | role << 8) and,
+//                     in the split form, r - r_O as the difference of the
+//                     images of r and r_O, 32 bytes
 //     pfixb  int4     pfix at the last list build (displacement check)
 //     nbr    int32 [maxnb][natom] column-major Verlet list (global j), nnb int32
 //   per cell: count int32, atoms int32 [cell_cap]
@@ -149,7 +151,9 @@ struct Dev {
     double *part, *kpart;
     dbl4 *x, *xo;
     dbl4 *v64, *f64, *h64, *dr64;
-    float4 *v32, *f32, *h32;
+    float4 *v32, *f32, *h32;     // v32: the quench's FIRE velocities (split form)
+    float4 *vf;                  // split form: MD velocities in FP32
+    int4 *po;                    // split form: fixed-point image of r_O (r - r_O = image difference)
     AtomRec *rec;                // fixed-point position + FP32 r - r_O
     int4 *pfixb;
     int *cellid, *nnb, *nbr, *cell_cnt, *cell_atoms;
@@ -241,33 +245,26 @@ __device__ __forceinline__ void normals32(uint4 w, float &n0, float &n1) {
     n1 = rad * fmaf(c, da, s);
 }
 
+// rint(q) mod 2^32 for |q| < 2^51: adding 1.5 2^52 leaves rint(q) (rounded to
+// nearest even, like rint) in the low bits of the sum's significand, and
+// 1.5 2^52 is a multiple of 2^32, so the sum's low word is the residue.  One
+// FP64 add instead of a 64-bit float-to-integer conversion.
+__device__ __forceinline__ int rint_low32(double q) { return __double2loint(q + 6755399441055744.0); }
+
 // Fixed-point image of one coordinate.
 __device__ __forceinline__ int fix_coord(const RepDev &R, int a, double x) {
     if (R.fx_scale[a] == 0.0) return 0;
-    long long q = __double2ll_rn((x - R.fx_origin[a]) * R.fx_scale[a]);
-    return (int)(unsigned int)(unsigned long long)q;
+    return rint_low32((x - R.fx_origin[a]) * R.fx_scale[a]);
 }
 
 __device__ __forceinline__ int4 fix_pos(const RepDev &R, dbl4 x, int w) {
     return make_int4(fix_coord(R, 0, x.x), fix_coord(R, 1, x.y), fix_coord(R, 2, x.z), w);
 }
 
-// r - r_O on the pair sweep's fixed-point grid (no origin, no wrap).  The
-// grid's int32 range covers |r - r_O| < L / 2^(k+1) >= 4 (rc + skin); beyond
-// it (an atom that has left its basin by that much without a new r_O) the
-// value saturates and *far is set.
-__device__ __forceinline__ int fix_disp(const RepDev &R, int a, double d, bool &far) {
-    if (R.fx_scale[a] == 0.0) return 0;
-    const double q = rint(d * R.fx_scale[a]);
-    if (!(fabs(q) < 2147483647.0)) {
-        far = true;
-        return q > 0.0 ? 2147483647 : -2147483647;
-    }
-    return (int)q;
-}
-__device__ __forceinline__ int4 fix_dr(const RepDev &R, dbl4 x, dbl4 xo, bool &far) {
-    return make_int4(fix_disp(R, 0, x.x - xo.x, far), fix_disp(R, 1, x.y - xo.y, far),
-                     fix_disp(R, 2, x.z - xo.z, far), 0);
+// Difference of two fixed-point images, per axis, modulo 2^32 (w = 0).
+__device__ __forceinline__ int4 img_diff(int4 a, int4 b) {
+    return make_int4((int)((unsigned)a.x - (unsigned)b.x), (int)((unsigned)a.y - (unsigned)b.y),
+                     (int)((unsigned)a.z - (unsigned)b.z), 0);
 }
 
 // Cell of an FP64 coordinate: exact integer map on periodic axes (the image

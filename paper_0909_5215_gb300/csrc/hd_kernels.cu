@@ -126,14 +126,13 @@ __global__ void k_init(Dev D, const int *draw_vel) {
     D.rec[i].p = p;
     D.pfixb[i] = p;
     const int role = (p.w >> 8) & 0xff;
-    if (D.prec == HD_FP64)
+    if (D.prec == HD_FP64) {
         D.dr64[i] = make_dbl4(x.x - xo.x, x.y - xo.y, x.z - xo.z, 0.0);
-    else
-        {
-            bool far = false;
-            D.rec[i].d = fix_dr(R, x, xo, far);
-            if (far) set_err(D, HD_ERR_NUMERIC, i, r);
-        }
+    } else {
+        const int4 po = fix_pos(R, xo, 0);
+        D.po[i] = po;
+        D.rec[i].d = img_diff(p, po);
+    }
     if (draw_vel[r]) {
         double v0 = 0, v1 = 0, v2 = 0;
         if (role == ROLE_MOBILE) {
@@ -147,7 +146,8 @@ __global__ void k_init(Dev D, const int *draw_vel) {
                 v2 = sd * z2;
             }
         }
-        D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
+        if (D.prec == HD_FP64) D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
+        else D.vf[i] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
     }
 }
 
@@ -287,13 +287,16 @@ __global__ void __launch_bounds__(128) k_cellsort(Dev D) {
 // lanes of the pair sweep leave the first shell, and later the cutoff, at
 // nearly the same k.  The row order is a deterministic function of the cell
 // lists (sorted by k_cellsort); reads return each row ascending in j.
+// ballot masks per warp of the list build: three per 32 staged candidates
+__host__ __device__ inline int nl_mask_words(const Dev &D) { return 3 * ((27 * D.cell_cap + 31) / 32); }
+
 struct NlSmem {
     int nst, tot, kc;
     int cell[27], off[28];
 };
 
-__device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSmem &M, int4 *sp, int *sj,
-                                               unsigned char *scls) {
+__device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSmem &M, int4 *sp,
+                                               unsigned *smask) {
     const RepDev &R = D.rep[r];
     const int cell0 = R.cell0 + c;
     const int m = min(D.cell_cnt[cell0], D.cell_cap);
@@ -380,10 +383,7 @@ __device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSme
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int idx = base + u * blockDim.x;
-                if (idx < tot) {
-                    sj[idx] = jj[u];
-                    sp[idx] = pp[u];
-                }
+                if (idx < tot) sp[idx] = make_int4(pp[u].x, pp[u].y, pp[u].z, jj[u]);   // w: the candidate's slot
             }
         }
     }
@@ -392,20 +392,21 @@ __device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSme
     const unsigned full = 0xffffffffu;
     const float lx = R.fx_lsb[0], ly = R.fx_lsb[1], lz = R.fx_lsb[2];
     const size_t stride = (size_t)D.natom;
-    unsigned char *cls = scls + (size_t)w * (27 * D.cell_cap);
+    // per warp: three ballot masks (classes A, B, C) per 32 candidates
+    unsigned *msk = smask + (size_t)w * nl_mask_words(D);
     for (int a = w; a < m; a += nw) {
         const int slot = M.off[M.kc] + a;
-        const int i = sj[slot];
         const int4 pi = sp[slot];
+        const int i = pi.w;
         int nA = 0, nB = 0, nC = 0;
         // pass 1: classify every candidate, count the classes
         for (int base = 0; base < tot; base += 32) {
             const int q = base + lane;
             int cl = 0;
             if (q < tot) {
-                const int j = sj[q];
+                const int4 pj = sp[q];
+                const int j = pj.w;
                 if (j != i) {
-                    const int4 pj = sp[q];
                     const float dx = (float)(int)((unsigned)pi.x - (unsigned)pj.x) * lx;
                     const float dy = (float)(int)((unsigned)pi.y - (unsigned)pj.y) * ly;
                     const float dz = (float)(int)((unsigned)pi.z - (unsigned)pj.z) * lz;
@@ -416,25 +417,29 @@ __device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSme
                     else in = exact_r2(R, D.x[i], D.x[j]) < D.rl2;
                     if (in) cl = r2 < R.rA2f ? 1 : (r2 < D.rc2_lo_f ? 2 : 3);
                 }
-                cls[q] = (unsigned char)cl;
             }
-            nA += __popc(__ballot_sync(full, cl == 1));
-            nB += __popc(__ballot_sync(full, cl == 2));
-            nC += __popc(__ballot_sync(full, cl == 3));
+            const unsigned mA = __ballot_sync(full, cl == 1), mB = __ballot_sync(full, cl == 2),
+                           mC = __ballot_sync(full, cl == 3);
+            if (lane == 0) {
+                msk[3 * (base >> 5)] = mA;
+                msk[3 * (base >> 5) + 1] = mB;
+                msk[3 * (base >> 5) + 2] = mC;
+            }
+            nA += __popc(mA);
+            nB += __popc(mB);
+            nC += __popc(mC);
         }
         __syncwarp();
         // pass 2: write the row as A | B | C, each block in candidate order
         int bA = 0, bB = nA, bC = nA + nB;
-        const unsigned below = (1u << lane) - 1u;
+        const unsigned below = (1u << lane) - 1u, bit = 1u << lane;
         for (int base = 0; base < tot; base += 32) {
-            const int q = base + lane;
-            const int cl = q < tot ? cls[q] : 0;
-            const unsigned mA = __ballot_sync(full, cl == 1), mB = __ballot_sync(full, cl == 2),
-                           mC = __ballot_sync(full, cl == 3);
+            const unsigned mA = msk[3 * (base >> 5)], mB = msk[3 * (base >> 5) + 1], mC = msk[3 * (base >> 5) + 2];
+            const int cl = (mA & bit) ? 1 : ((mB & bit) ? 2 : ((mC & bit) ? 3 : 0));
             if (cl) {
                 const int pos = cl == 1 ? bA + __popc(mA & below) : (cl == 2 ? bB + __popc(mB & below)
                                                                              : bC + __popc(mC & below));
-                if (pos < cap) D.nbr[(size_t)pos * stride + i] = sj[q];
+                if (pos < cap) D.nbr[(size_t)pos * stride + i] = sp[base + lane].w;
             }
             bA += __popc(mA);
             bB += __popc(mB);
@@ -450,24 +455,21 @@ __device__ __forceinline__ void dev_nlist_cell(const Dev &D, int r, int c, NlSme
     __syncthreads();  // the staging buffers are reused by the next cell
 }
 
-__device__ __forceinline__ void nl_smem_carve(const Dev &D, char *base, int4 *&sp, int *&sj, unsigned char *&scls) {
-    const int cmax = 27 * D.cell_cap;
+__device__ __forceinline__ void nl_smem_carve(const Dev &D, char *base, int4 *&sp, unsigned *&smask) {
     sp = reinterpret_cast<int4 *>(base);
-    sj = reinterpret_cast<int *>(base + (size_t)cmax * sizeof(int4));
-    scls = reinterpret_cast<unsigned char *>(base + (size_t)cmax * (sizeof(int4) + sizeof(int)));
+    smask = reinterpret_cast<unsigned *>(base + (size_t)27 * D.cell_cap * sizeof(int4));
 }
 
 __global__ void __launch_bounds__(128) k_nlist(Dev D) {
     extern __shared__ __align__(16) char nl_smem[];
     __shared__ NlSmem M;
     int4 *sp;
-    int *sj;
-    unsigned char *scls;
-    nl_smem_carve(D, nl_smem, sp, sj, scls);
+    unsigned *smask;
+    nl_smem_carve(D, nl_smem, sp, smask);
     const int n = D.rb_meta[0], total = D.rb_meta[1];
     for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
         const int k = rb_find(D.rb_off, n, idx);
-        dev_nlist_cell(D, D.rb_list[k], idx - D.rb_off[k], M, sp, sj, scls);
+        dev_nlist_cell(D, D.rb_list[k], idx - D.rb_off[k], M, sp, smask);
     }
 }
 
@@ -1183,6 +1185,29 @@ __device__ __forceinline__ void post_move(const Dev &D, const RepDev &R, int r, 
         set_err(D, HD_ERR_NUMERIC, i, r);
 }
 
+// Split form: the new fixed-point image and r - r_O as the difference of
+// images, in one 32-byte record store; then the checks of post_move.  r - r_O
+// wraps at L / 2^(k+1) >= 4 (rc + skin); an atom is reported (HD_ERR_NUMERIC)
+// when it has moved 3/4 of that from its r_O.
+__device__ __forceinline__ void post_move32(const Dev &D, const RepDev &R, int r, int i, dbl4 x, int4 p) {
+    const int4 q = fix_pos(R, x, p.w);
+    const int4 d = img_diff(q, D.po[i]);
+    AtomRec a;
+    a.p = q;
+    a.d = d;
+    D.rec[i] = a;
+    const int4 b = D.pfixb[i];
+    const float ex = (float)(int)((unsigned)q.x - (unsigned)b.x) * R.fx_lsb[0];
+    const float ey = (float)(int)((unsigned)q.y - (unsigned)b.y) * R.fx_lsb[1];
+    const float ez = (float)(int)((unsigned)q.z - (unsigned)b.z) * R.fx_lsb[2];
+    if (ex * ex + ey * ey + ez * ez > D.half_skin2_f) D.rebuild[r] = 1;
+    const double zv = R.vert == 2 ? x.z : x.y;
+    const int lim = 3 << 29;
+    if (!(fabs(zv - R.fx_origin[R.vert]) < R.open_lim) || !isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z) ||
+        abs(d.x) > lim || abs(d.y) > lim || abs(d.z) > lim)
+        set_err(D, HD_ERR_NUMERIC, i, r);
+}
+
 __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, const Scal &C) {
     const int r = D.tile_rep[t];
     const RepDev &R = D.rep[r];
@@ -1276,7 +1301,8 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
 }
 
 __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, const Scal &C) {
-    // split form: FP32 forces, FP64 velocities and positions
+    // split form: FP32 forces and velocities, FP64 positions; r - r_O from
+    // the fixed-point images of r and r_O
     const int r = D.tile_rep[t];
     const RepDev &R = D.rep[r];
     const bool act = threadIdx.x < D.tile_n[t];
@@ -1287,65 +1313,68 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
     float kin = 0.f;
     if (role != ROLE_FIXED) {
         const double hh = 0.5 * D.dt;
-        dbl4 v = D.v64[i];
+        const float hf = (float)hh;
+        float4 v = D.vf[i];
         dbl4 x = D.x[i];
         if (role == ROLE_MOBILE) {
             const float4 F = D.f32[i], H = D.h32[i];
             const float4 dr = make_float4((float)ai.d.x * R.fx_lsb[0], (float)ai.d.y * R.fx_lsb[1],
                                           (float)ai.d.z * R.fx_lsb[2], 0.f);
             const float ca = (float)C.ca, cb = (float)C.cb;
-            double Fx = (double)fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
-            double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
-            double Fz = (double)fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
-            if (C.ce != 0.0) {               // eigenvalue bias (Eq. 13, Eq. 15), FP64
+            float Fx = fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
+            float Fy = fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
+            float Fz = fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
+            if (C.ce != 0.0) {               // eigenvalue bias (Eq. 13, Eq. 15), from FP64 grad epsilon
                 const dbl4 g = D.eg[i];
-                Fx += C.ce * g.x;
-                Fy += C.ce * g.y;
-                Fz += C.ce * g.z;
+                Fx += (float)(C.ce * g.x);
+                Fy += (float)(C.ce * g.y);
+                Fz += (float)(C.ce * g.z);
             }
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
-            if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+            const float sc = (float)C.nhc_scale;
+            if (mode & MODE_KIN) kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
             if (mode & MODE_SCALE) {
                 if (chain) {
-                    v.x *= C.nhc_scale;
-                    v.y *= C.nhc_scale;
-                    v.z *= C.nhc_scale;
+                    v.x *= sc;
+                    v.y *= sc;
+                    v.z *= sc;
                 }
-                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+                kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
             if (mode & MODE_CLOSE) {
-                v.x += hh * Fx;
-                v.y += hh * Fy;
-                if (three) v.z += hh * Fz;
-                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+                v.x = fmaf(hf, Fx, v.x);
+                v.y = fmaf(hf, Fy, v.y);
+                if (three) v.z = fmaf(hf, Fz, v.z);
+                kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
             }
             if (mode & MODE_OPEN) {
                 if (chain && (mode & MODE_NHC)) {
-                    v.x *= C.nhc_scale;
-                    v.y *= C.nhc_scale;
-                    v.z *= C.nhc_scale;
+                    v.x *= sc;
+                    v.y *= sc;
+                    v.z *= sc;
                 }
-                v.x += hh * Fx;
-                v.y += hh * Fy;
-                if (three) v.z += hh * Fz;
-                const double ax = v.x, ay = v.y, az = v.z;
+                v.x = fmaf(hf, Fx, v.x);
+                v.y = fmaf(hf, Fy, v.y);
+                if (three) v.z = fmaf(hf, Fz, v.z);
+                const float ax = v.x, ay = v.y, az = v.z;
                 if (!chain) {
                     float n0, n1, n2, n3;
                     normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
-                    v.x = R.c_ou * v.x + R.s_ou * (double)n0;
-                    v.y = R.c_ou * v.y + R.s_ou * (double)n1;
+                    v.x = fmaf(R.c_ouf, v.x, R.s_ouf * n0);
+                    v.y = fmaf(R.c_ouf, v.y, R.s_ouf * n1);
                     if (three) {
                         normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
-                        v.z = R.c_ou * v.z + R.s_ou * (double)n2;
+                        v.z = fmaf(R.c_ouf, v.z, R.s_ouf * n2);
                     }
                 }
-                x.x += hh * (ax + v.x);
-                x.y += hh * (ay + v.y);
-                if (three) x.z += hh * (az + v.z);
+                // the two half drifts A of BAOAB, in FP64
+                x.x += hh * (double)(ax + v.x);
+                x.y += hh * (double)(ay + v.y);
+                if (three) x.z += hh * (double)(az + v.z);
             }
         } else {
-            if (mode & MODE_CLOSE) v = make_dbl4(C.vb_mid[0], C.vb_mid[1], C.vb_mid[2], 0.0);
+            if (mode & MODE_CLOSE) v = make_float4((float)C.vb_mid[0], (float)C.vb_mid[1], (float)C.vb_mid[2], 0.f);
             if (mode & MODE_OPEN) {
                 x.x += hh * C.vb_new[0];
                 x.y += hh * C.vb_new[1];
@@ -1353,19 +1382,13 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
                 x.x += hh * C.vb_new[0];
                 x.y += hh * C.vb_new[1];
                 x.z += hh * C.vb_new[2];
-                v = make_dbl4(C.vb_new[0], C.vb_new[1], C.vb_new[2], 0.0);
+                v = make_float4((float)C.vb_new[0], (float)C.vb_new[1], (float)C.vb_new[2], 0.f);
             }
         }
-        D.v64[i] = v;
+        D.vf[i] = v;
         if (mode & MODE_OPEN) {
             D.x[i] = x;
-            const dbl4 xo = D.xo[i];
-            {
-                bool far = false;
-                D.rec[i].d = fix_dr(R, x, xo, far);
-                if (far) set_err(D, HD_ERR_NUMERIC, i, r);
-            }
-            post_move(D, R, r, i, x, p);
+            post_move32(D, R, r, i, x, p);
         }
     }
     if (mode & (MODE_CLOSE | MODE_KIN | MODE_SCALE)) {
@@ -1588,9 +1611,9 @@ __global__ void k_adopt(Dev Q, Dev M, const int *adopt) {
     const dbl4 x = M.x[i];
     if (M.prec == HD_FP64) M.dr64[i] = make_dbl4(x.x - q.x, x.y - q.y, x.z - q.z, 0.0);
     else {
-        bool far = false;
-        M.rec[i].d = fix_dr(M.rep[r], x, make_dbl4(q.x, q.y, q.z, 0.0), far);
-        if (far) set_err(M, HD_ERR_NUMERIC, i, r);
+        const int4 po = fix_pos(M.rep[r], make_dbl4(q.x, q.y, q.z, 0.0), 0);
+        M.po[i] = po;
+        M.rec[i].d = img_diff(M.rec[i].p, po);
     }
 }
 
@@ -1652,9 +1675,8 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
     __shared__ NlSmem M;
     extern __shared__ __align__(16) char nl_smem[];
     int4 *sp;
-    int *sj;
-    unsigned char *scls;
-    nl_smem_carve(D, nl_smem, sp, sj, scls);
+    unsigned *smask;
+    nl_smem_carve(D, nl_smem, sp, smask);
     if (threadIdx.x == 0) {
         S = D.st[r];
         C = D.sc[r];
@@ -1719,7 +1741,7 @@ __global__ void __launch_bounds__(128, 4) k_persist(Dev D, int nsteps) {
                 if (leader) D.rebuild[r] = 0;
             }
             // rows are built cell by cell, so a CTA's tiles take rows other CTAs wrote
-            for (int c = me; c < R.ncell; c += nc) dev_nlist_cell(D, r, c, M, sp, sj, scls);
+            for (int c = me; c < R.ncell; c += nc) dev_nlist_cell(D, r, c, M, sp, smask);
             if (!grp_barrier(D, r, nc, epoch)) return;
         }
         for (int t = R.tile0 + me; t < R.tile0 + R.ntile; t += nc) {
@@ -1755,8 +1777,7 @@ static inline int nthr(const Dev &D) { return D.block; }
 // of up to 27 cells of cell_cap candidates (classes: one byte per candidate
 // for each of the warps of a 128-thread CTA).
 size_t nl_smem_bytes(const Dev &D) {
-    const size_t cmax = 27 * (size_t)D.cell_cap;
-    return cmax * (sizeof(int4) + sizeof(int)) + cmax * 4;
+    return 27 * (size_t)D.cell_cap * sizeof(int4) + 4 * (size_t)nl_mask_words(D) * sizeof(unsigned);
 }
 // the persistent kernel runs the list build and the pair sweep in one launch
 static size_t persist_smem_bytes(const Dev &D) {
