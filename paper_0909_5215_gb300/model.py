@@ -321,10 +321,11 @@ def paper3d(**kw) -> Replica:
 # Workloads.  Each returns (list[Replica], Params).
 # --------------------------------------------------------------------------
 
-def afm2d_plain(seed: int = 20250909):
-    """2-D model, one slider position, no bias, FP64; ~421 atoms, T=0.05."""
+def afm2d_plain(seed: int = 20250909, prec: int = 0):
+    """2-D model, one slider position, no bias; ~421 atoms, T=0.05 (the plain
+    FP64 configuration; prec selects the form)."""
     r = afm2d(kT=0.05, gamma=1.0, k_spring=1.0, f_normal=1.0, rep_id=0, eps=PAPER_EPS_2D)
-    return [r], Params(bias_on=0, seed=seed, prec=0)
+    return [r], Params(bias_on=0, seed=seed, prec=prec)
 
 
 def afm2d_hyper(n_rep: int = 16, spacing: float = 0.05, prec: int = 1, seed: int = 20250909):

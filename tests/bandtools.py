@@ -12,13 +12,14 @@ import math
 import numpy as np
 
 
-def run_band_prerun(oracle_mod, reps, p, sample, steps=100, q_lo=0.1, q_hi=0.9, skip_frac=0.2):
+def run_band_prerun(oracle_mod, reps, p, sample, steps=100, q_lo=0.1, q_hi=0.9, skip_frac=0.2, draw=True):
     """Set sig_lo, sig_hi of every replica: sampled replicas get the q_lo..q_hi
     quantiles of sigma over an unbiased oracle pre-run (the first skip_frac of
     the steps left out); the others copy the band of the sampled replica of
-    the same dimension whose size is closest on a log scale."""
+    the same dimension whose size is closest on a log scale.  draw: start from
+    Maxwell-Boltzmann velocities (True) or the replicas' own (None)."""
     p0 = dataclasses.replace(p, bias_on=0)
-    ors = [oracle_mod.OracleReplica(reps[k], p0, draw_velocities=True) for k in sample]
+    ors = [oracle_mod.OracleReplica(reps[k], p0, draw_velocities=draw) for k in sample]
     sig = []
     for s in range(steps):
         oracle_mod.run_batch(ors, 1)
