@@ -174,13 +174,19 @@ hd_status hd_step(hd_ctx *ctx, int n_steps);
  * on a mobile atom or the rigid body is below ftol or max_iter updates were
  * made.  A replica whose quenched positions lie more than theta from r_O
  * (any atom, minimum image) is flagged as having made a transition
- * (Sec. 2.3).  adopt: 0 keep r_O; 1 set r_O to the quenched positions of
- * flagged replicas; 2 of every replica.  Only a replica whose quench reached
- * ftol adopts: an unconverged quench is no basin minimum (HD_OBS_QCONV says
- * which converged).  h_flags [n_rep] (may be NULL) receives the flags; the
- * call synchronises the stream.  The MD state is not changed. */
+ * (Sec. 2.3).  ftol_stay > ftol (0: off) stops a replica's quench earlier,
+ * once its largest force is below ftol_stay while every atom lies within
+ * theta/2 of r_O: the state is then well inside the transition threshold
+ * and stays unflagged (HD_OBS_QCONV = 2); a replica that has moved further
+ * runs on to ftol.  ftol_stay needs a finite theta > 0.  adopt: 0 keep r_O;
+ * 1 set r_O to the quenched positions of flagged replicas; 2 of every
+ * replica.  Only a replica whose quench reached ftol adopts: an unconverged
+ * quench is no basin minimum.  h_flags [n_rep] (may be NULL) receives the
+ * flags; the call synchronises the stream.  The MD state is not changed.
+ * HD_ERR_ARG: method not 0 or 1, ftol <= 0, max_iter < 0, step_size <= 0,
+ * adopt outside 0..2, or ftol_stay neither 0 nor above ftol. */
 hd_status hd_quench(hd_ctx *ctx, int method, double ftol, int max_iter, double step_size,
-                    double theta, int adopt, int32_t *h_flags);
+                    double theta, double ftol_stay, int adopt, int32_t *h_flags);
 
 /* Copy one field of one replica to host memory (synchronises the stream).
  * bytes must equal the field's size for that replica. */
@@ -208,7 +214,8 @@ enum {
     HD_OBS_NDV_ZERO = 24,      /* steps taken so far with DeltaV = 0 (sigma <= sigma_L) */
     HD_OBS_NDV_BAND = 25,      /* ... with 0 < DeltaV < DeltaV_max                    */
     HD_OBS_NDV_MAX = 26,       /* ... with DeltaV = DeltaV_max (sigma >= sigma_U)      */
-    HD_OBS_QCONV = 27,         /* 1 if the last quench reached ftol, else 0            */
+    HD_OBS_QCONV = 27,         /* last quench: 1 reached ftol, 2 stopped inside its   *
+                                *  basin at ftol_stay, 0 stopped at max_iter           */
     HD_OBS_XS = 28,            /* slider x_S of the current configuration             */
     HD_OBS_NHC_E = 29,         /* chain energy sum Q v^2/2 + N_f kT xi_1 + kT sum xi_j */
     HD_OBS_EIG = 30,           /* epsilon of Eq. 15 (eigenvalue bias)                 */

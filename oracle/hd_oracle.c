@@ -1088,8 +1088,25 @@ static void or_qforce(const or_rep *R, const or_params *P, const double *xq, con
     *fmax = sqrt(m);
 }
 
-int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_iter,
-              double step_size, double *xq, double *fmax_out) {
+/* Largest displacement of xq from r_O over all atoms, squared (minimum image). */
+static double or_maxdisp2(const or_rep *R, const double *xq) {
+    double m = 0.0, dr[3];
+    for (int i = 0; i < R->n; ++i) {
+        or_disp(R, xq, i, dr);
+        double q = dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2];
+        if (q > m) m = q;
+    }
+    return m;
+}
+
+/* The quench serves the transition test (Sec. 2.3), whose answer is a
+ * displacement from r_O compared with theta.  Reading: a replica whose every
+ * atom already lies within keep (< theta) of r_O and whose largest force is
+ * below ftol_stay (> ftol) has not left its basin, and its quench stops there;
+ * one that has not reached both goes on to ftol.  ftol_stay = 0 turns the
+ * early stop off. */
+int or_quench_gated(or_rep *R, const or_params *P, int method, double ftol, double ftol_stay, double keep,
+                    int max_iter, double step_size, double *xq, double *fmax_out) {
     int n = R->n, nr = or_nrig(R), D = R->dim;
     int *nnb = malloc(sizeof(int) * n), *nbr = malloc(sizeof(int) * (size_t)n * R->maxnb);
     double *xb = malloc(sizeof(double) * 3 * n), *f = malloc(sizeof(double) * 3 * n);
@@ -1115,6 +1132,7 @@ int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_it
         }
         or_qforce(R, P, xq, nnb, nbr, f, fb, &fmax);
         if (fmax < ftol) break;
+        if (ftol_stay > 0.0 && fmax < ftol_stay && or_maxdisp2(R, xq) < keep * keep) break;
         if (!(fmax < 1e30)) break;            /* diverged (step too large for the stiffest mode) */
         if (method == 0) {
             for (int i = 0; i < n; ++i) {
@@ -1179,12 +1197,23 @@ int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_it
     return it;
 }
 
+int or_quench(or_rep *R, const or_params *P, int method, double ftol, int max_iter,
+              double step_size, double *xq, double *fmax_out) {
+    return or_quench_gated(R, P, method, ftol, 0.0, 0.0, max_iter, step_size, xq, fmax_out);
+}
+
 int or_quench_batch(or_rep *reps, int nrep, const or_params *P, int method, double ftol,
                     int max_iter, double step_size, double **xq, double *fmax_out, int *iters) {
+    return or_quench_batch_gated(reps, nrep, P, method, ftol, 0.0, 0.0, max_iter, step_size, xq, fmax_out, iters);
+}
+
+int or_quench_batch_gated(or_rep *reps, int nrep, const or_params *P, int method, double ftol, double ftol_stay,
+                          double keep, int max_iter, double step_size, double **xq, double *fmax_out, int *iters) {
     int r;
 #pragma omp parallel for schedule(dynamic, 1)
     for (r = 0; r < nrep; ++r)
-        iters[r] = or_quench(&reps[r], P, method, ftol, max_iter, step_size, xq[r], &fmax_out[r]);
+        iters[r] = or_quench_gated(&reps[r], P, method, ftol, ftol_stay, keep, max_iter, step_size, xq[r],
+                                   &fmax_out[r]);
     return 0;
 }
 

@@ -112,6 +112,11 @@ int    or_quench(or_rep *R, const or_params *P, int method, double ftol, int max
                  double step_size, double *xq, double *fmax_out);
 int    or_quench_batch(or_rep *reps, int nrep, const or_params *P, int method, double ftol,
                        int max_iter, double step_size, double **xq, double *fmax_out, int *iters);
+int    or_quench_gated(or_rep *R, const or_params *P, int method, double ftol, double ftol_stay, double keep,
+                       int max_iter, double step_size, double *xq, double *fmax_out);
+int    or_quench_batch_gated(or_rep *reps, int nrep, const or_params *P, int method, double ftol,
+                             double ftol_stay, double keep, int max_iter, double step_size, double **xq,
+                             double *fmax_out, int *iters);
 int    or_transition(const or_rep *R, const double *xq, double theta, double *maxdisp);
 double or_lj3(double r, double eps, double sig);
 void   or_project(const or_rep *R, double *u);

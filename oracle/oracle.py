@@ -102,6 +102,11 @@ def lib():
         L.or_quench.restype = C.c_int
         L.or_quench_batch.argtypes = [rp, C.c_int, pp, C.c_int, C.c_double, C.c_int, C.c_double,
                                       C.POINTER(dp), dp, ip]
+        L.or_quench_gated.argtypes = [rp, pp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                                      dp, dp]
+        L.or_quench_gated.restype = C.c_int
+        L.or_quench_batch_gated.argtypes = [rp, C.c_int, pp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                            C.c_double, C.POINTER(dp), dp, ip]
         L.or_transition.argtypes = [rp, dp, C.c_double, dp]
         L.or_transition.restype = C.c_int
         L.or_num_threads.restype = C.c_int
@@ -281,13 +286,15 @@ class OracleReplica:
     def run(self, nsteps):
         lib().or_run(C.byref(self.s), C.byref(self.P), int(nsteps))
 
-    def quench(self, method=0, ftol=1e-6, max_iter=20000, step_size=None):
+    def quench(self, method=0, ftol=1e-6, max_iter=20000, step_size=None, ftol_stay=0.0, keep=0.0):
+        """Quench a copy of the positions; with ftol_stay > 0 the quench also
+        stops once max|F| < ftol_stay with every atom within keep of r_O."""
         if step_size is None:
             step_size = (0.002 if method == 0 else 0.01)
         xq = np.zeros((self.n, 3))
         fmax = np.zeros(1)
-        it = lib().or_quench(C.byref(self.s), C.byref(self.P), int(method), float(ftol), int(max_iter),
-                             float(step_size), _dp(xq), _dp(fmax))
+        it = lib().or_quench_gated(C.byref(self.s), C.byref(self.P), int(method), float(ftol), float(ftol_stay),
+                                   float(keep), int(max_iter), float(step_size), _dp(xq), _dp(fmax))
         return xq, int(it), float(fmax[0])
 
     # ---- eigenvalue bias (Eq. 13, Eq. 15) ----
@@ -354,9 +361,10 @@ def num_threads():
     return lib().or_num_threads()
 
 
-def quench_batch(reps, method=1, ftol=1e-6, max_iter=20000, step_size=None):
+def quench_batch(reps, method=1, ftol=1e-6, max_iter=20000, step_size=None, ftol_stay=0.0, keep=0.0):
     """Quench a list of OracleReplica in parallel (OpenMP over replicas);
-    returns the quenched positions, iteration counts and final max forces."""
+    returns the quenched positions, iteration counts and final max forces.
+    ftol_stay, keep: the early stop of OracleReplica.quench."""
     if step_size is None:
         step_size = (0.002 if method == 0 else 0.01)
     n = len(reps)
@@ -369,6 +377,7 @@ def quench_batch(reps, method=1, ftol=1e-6, max_iter=20000, step_size=None):
     ptrs = (C.POINTER(C.c_double) * n)(*[_dp(x) for x in xq])
     fmax = np.zeros(n)
     iters = np.zeros(n, np.int32)
-    lib().or_quench_batch(arr, n, C.byref(reps[0].P), int(method), float(ftol), int(max_iter), float(step_size),
-                          ptrs, _dp(fmax), iters.ctypes.data_as(C.POINTER(C.c_int)))
+    lib().or_quench_batch_gated(arr, n, C.byref(reps[0].P), int(method), float(ftol), float(ftol_stay), float(keep),
+                                int(max_iter), float(step_size), ptrs, _dp(fmax),
+                                iters.ctypes.data_as(C.POINTER(C.c_int)))
     return xq, iters, fmax

@@ -37,7 +37,7 @@ struct Plan {
     size_t o_rep, o_st, o_sc, o_trep, o_tstart, o_tn, o_part, o_qpart, o_kpart;
     size_t o_x, o_xo, o_xq, o_v, o_vq, o_f, o_fq, o_h, o_dr;
     size_t o_pfix, o_pfixb, o_qpfix, o_qpfixb, o_cellid, o_nnb, o_nbr, o_ccnt, o_catoms;
-    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_drawvel, o_adopt, o_orig, o_rboff, o_rbaoff, o_rblist, o_rbmeta;
+    size_t o_rebuild, o_qrebuild, o_err, o_bar, o_qdisp, o_qgate, o_drawvel, o_adopt, o_orig, o_rboff, o_rbaoff, o_rblist, o_rbmeta;
     size_t o_ctarep, o_pgfirst, o_pgcount, o_boff, o_bj;
     size_t o_eq, o_ev, o_ew, o_eg, o_ealpha, o_ebeta, o_ey, o_ecoef, o_epart, o_po;
     long long eig_q = 0, eig_t = 0;     // dbl4 entries of all Krylov bases, doubles of all tridiagonals
@@ -385,6 +385,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_err = take(cur, 4 * 4);
     P.o_bar = take(cur, R * 2 * 4);
     P.o_qdisp = take(cur, R * 8);
+    P.o_qgate = take(cur, R * 8);
     P.o_drawvel = take(cur, R * 4);
     P.o_adopt = take(cur, R * 4);
     P.o_orig = take(cur, N * 4);
@@ -582,6 +583,7 @@ void fill_dev(hd_ctx *c) {
     D.err = at<int>(b, P.o_err);
     D.bar = at<unsigned int>(b, P.o_bar);
     D.qdisp = at<unsigned long long>(b, P.o_qdisp);
+    D.qgate = at<unsigned long long>(b, P.o_qgate);
     D.orig = at<int>(b, P.o_orig);
     D.rb_off = at<int>(b, P.o_rboff);
     D.rb_aoff = at<int>(b, P.o_rbaoff);
@@ -906,7 +908,7 @@ hd_status hd_set_slider(hd_ctx *c, const double *slider, int requench_ref) {
     // FIRE from dt0 = 0.005 (fastest on thermal LJ states); the rigid body's
     // force, a sum over its atoms' FP32 pair forces, levels off near 4e-4 in
     // the split form, so that form quenches to 1e-3
-    if (requench_ref) return hd_quench(c, 1, c->P.prec == HD_FP64 ? 1e-6 : 1e-3, 20000, 0.005, 1e300, 2, nullptr);
+    if (requench_ref) return hd_quench(c, 1, c->P.prec == HD_FP64 ? 1e-6 : 1e-3, 20000, 0.005, 1e300, 0.0, 2, nullptr);
     return HD_OK;
 }
 
@@ -1011,18 +1013,23 @@ hd_status hd_step(hd_ctx *c, int n_steps) {
     return HD_OK;
 }
 
-hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double step_size, double theta, int adopt,
-                    int32_t *h_flags) {
+hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double step_size, double theta,
+                    double ftol_stay, int adopt, int32_t *h_flags) {
     if (!c) return HD_ERR_ARG;
     if (c->status != HD_OK) return HD_ERR_STATE;
     if ((method != 0 && method != 1) || !(ftol > 0.0) || max_iter < 0 || !(step_size > 0.0) || adopt < 0 || adopt > 2)
         return fail(c, HD_ERR_ARG, "bad quench arguments");
+    if (!(ftol_stay == 0.0 || (ftol_stay > ftol && theta > 0.0 && std::isfinite(theta))))
+        return fail(c, HD_ERR_ARG, "ftol_stay must be 0, or above ftol with a finite theta > 0");
     Dev &Q = c->Q;
     Q.q_method = method;
     Q.q_ftol = ftol;
     Q.q_step = step_size;
     Q.q_theta = theta;
+    Q.q_ftol_stay = ftol_stay;
+    Q.q_keep2 = 0.25 * theta * theta;
     const int R = c->P.nrep;
+    if (ftol_stay > 0.0) CK(cudaMemsetAsync(Q.qgate, 0, (size_t)R * 8, c->s));
     launch_qinit(Q, c->D, c->s);
     c->launches += 1;
     std::vector<RepState> st(R);
@@ -1033,7 +1040,7 @@ hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double ste
     cudaGraphExec_t qg = nullptr;
     if (c->s != nullptr && cs == cudaStreamCaptureStatusNone) {
         char key[128];
-        snprintf(key, sizeof key, "%d/%.17g/%.17g/%d", method, ftol, step_size, max_iter);
+        snprintf(key, sizeof key, "%d/%.17g/%.17g/%d/%.17g/%.17g", method, ftol, step_size, max_iter, ftol_stay, theta);
         auto it = c->qgraphs.find(key);
         if (it == c->qgraphs.end()) {
             if (c->qgraphs.size() >= 8) {
@@ -1080,10 +1087,10 @@ hd_status hd_quench(hd_ctx *c, int method, double ftol, int max_iter, double ste
         c->qflag[r] = std::sqrt(m) > theta;
         // st[] holds the state after the last chunk: q_fmax is that of the
         // final positions (the iteration that found fmax < ftol moved nothing)
-        c->qconv[r] = st[r].q_fmax < ftol;
+        c->qconv[r] = st[r].q_fmax < ftol ? 1 : (st[r].q_stay ? 2 : 0);
         if (h_flags) h_flags[r] = c->qflag[r];
         // an unconverged quench is no basin minimum: it never becomes r_O
-        ad[r] = c->qconv[r] && (adopt == 2 || (adopt == 1 && c->qflag[r]));
+        ad[r] = c->qconv[r] == 1 && (adopt == 2 || (adopt == 1 && c->qflag[r]));
         any |= ad[r] != 0;
     }
     if (any) {

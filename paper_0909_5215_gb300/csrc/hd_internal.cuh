@@ -122,6 +122,7 @@ struct RepState {
     // quench
     double q_dt, q_alpha, q_vb[3], q_fmax, q_disp;
     int q_npos, q_iter, q_done, q_flag;
+    int q_stay, pad_q;           // the quench stopped inside its basin (at ftol_stay, not ftol)
 };
 
 struct Scal {
@@ -141,6 +142,7 @@ struct Dev {
     int nrep, ntile, natom, maxnb, cell_cap, ncell, prec, bias_on, block;
     int q_method, max_cells;        // max_cells: largest cell count of one replica
     double dt, rc2, rl2, half_skin2, q_ftol, q_step, q_theta;
+    double q_ftol_stay, q_keep2;    // quench: early stop inside the basin (0: off), (theta/2)^2
     float rc2f, rl2_lo_f, rl2_hi_f, half_skin2_f;
     float rc2_lo_f, rc2_hi_f;    // rc^2 (1 -+ 2^-20): band decided in FP64
     uint32_t seed_lo, seed_hi;
@@ -161,6 +163,7 @@ struct Dev {
     int *err;                    // [0] first error code, [1] atom, [2] replica
     unsigned int *bar;           // per replica barrier counters (persistent driver)
     unsigned long long *qdisp;   // per replica max |x_q - r_O|^2 (bits of the double)
+    unsigned long long *qgate;   // per replica max |x_q - r_O|^2 of the current quench iterate
     const int *orig;             // per slot: index of the atom in its replica's input
     int *rb_list;                // replicas whose list is rebuilt, ascending (count rb_meta[0])
     int *rb_off, *rb_aoff;       // [count + 1] first compacted cell / atom of each of them

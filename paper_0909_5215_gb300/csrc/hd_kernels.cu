@@ -1406,6 +1406,29 @@ __global__ void __launch_bounds__(256) k_update32(Dev D, int mode) {
 }
 
 // ---------------------------------------------------------------- quench
+// |x - r_O|^2 in FP64, in the transition test's operation order.  Positions
+// and r_O are never wrapped, so below L/2 per axis this is the minimum-image
+// value bit for bit; beyond it it is larger, which only delays an early stop.
+__device__ __forceinline__ double disp2(dbl4 a, dbl4 b) {
+    const double d0 = __dsub_rn(a.x, b.x), d1 = __dsub_rn(a.y, b.y), d2 = __dsub_rn(a.z, b.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+}
+
+// Largest m over the CTA into qgate[r] (non-negative doubles order as their
+// bit patterns).  Every thread of the CTA calls it.
+__device__ __forceinline__ void gate_max(const Dev &D, int r, double m) {
+    __shared__ double sm[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    m = warp_max(m);
+    if (lane == 0) sm[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = sm[0];
+        for (int k = 1; k < nw; ++k) a = fmax(a, sm[k]);
+        atomicMax(D.qgate + r, (unsigned long long)__double_as_longlong(a));
+    }
+}
+
 __global__ void k_qinit(Dev Q, Dev M) {
     // Q: quench view (x = copy), M: MD view
     const int t = blockIdx.x, r = Q.tile_rep[t];
@@ -1417,17 +1440,23 @@ __global__ void k_qinit(Dev Q, Dev M) {
         S.q_iter = 0;
         S.q_done = 0;
         S.q_flag = 0;
+        S.q_stay = 0;
         S.q_fmax = 0.0;
         S.q_vb[0] = S.q_vb[1] = S.q_vb[2] = 0.0;
         Q.qdisp[r] = 0ull;
         Q.rebuild[r] = 2;
     }
-    if (threadIdx.x >= Q.tile_n[t]) return;
-    const int i = Q.tile_start[t] + threadIdx.x;
-    Q.x[i] = M.x[i];
-    Q.rec[i].p = M.rec[i].p;
-    if (Q.prec == HD_FP64) Q.v64[i] = make_dbl4(0, 0, 0, 0);
-    else Q.v32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    double m = 0.0;
+    if (threadIdx.x < Q.tile_n[t]) {
+        const int i = Q.tile_start[t] + threadIdx.x;
+        const dbl4 x = M.x[i];
+        Q.x[i] = x;
+        Q.rec[i].p = M.rec[i].p;
+        if (Q.prec == HD_FP64) Q.v64[i] = make_dbl4(0, 0, 0, 0);
+        else Q.v32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (Q.q_ftol_stay > 0.0) m = disp2(x, Q.xo[i]);
+    }
+    if (Q.q_ftol_stay > 0.0) gate_max(Q, r, m);
 }
 
 // Convergence test and FIRE bookkeeping (reading of Bitzek et al. 2006: mix
@@ -1468,8 +1497,17 @@ __global__ void k_qscalar(Dev D, int max_iter) {
     }
     const double fmax_ = sqrt(fm2);
     S.q_fmax = fmax_;
-    if (fmax_ < D.q_ftol || S.q_iter >= max_iter) {
+    // early stop inside the basin: every atom within theta/2 of r_O and the
+    // force below ftol_stay rule a transition out (Sec. 2.3 transition test)
+    bool stay = false;
+    if (D.q_ftol_stay > 0.0) {
+        const double g2 = __longlong_as_double((long long)D.qgate[r]);
+        D.qgate[r] = 0ull;
+        stay = fmax_ < D.q_ftol_stay && g2 < D.q_keep2;
+    }
+    if (fmax_ < D.q_ftol || stay || S.q_iter >= max_iter) {
         S.q_done = 1;
+        S.q_stay = stay && !(fmax_ < D.q_ftol);
         C.q_active = 0;
         return;
     }
@@ -1518,7 +1556,7 @@ __global__ void k_qscalar(Dev D, int max_iter) {
 // Per-atom quench move.  SD: x += a F (body: a F_body / n_rig).  FIRE: mix,
 // or zero, the velocity, then a semi-implicit Euler step.
 template <typename V4>
-__device__ __forceinline__ void qmove(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
+__device__ __forceinline__ dbl4 qmove(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
                                       double fx, double fy, double fz, V4 *vq) {
     dbl4 x = D.x[i];
     const int dim = R.dim;
@@ -1563,25 +1601,33 @@ __device__ __forceinline__ void qmove(const Dev &D, const RepDev &R, const Scal 
     }
     D.x[i] = x;
     post_move(D, R, r, i, x, p);
+    return x;
 }
 
 __global__ void __launch_bounds__(256) k_qupdate(Dev D) {
     const int t = blockIdx.x, r = D.tile_rep[t];
     const Scal &C = D.sc[r];
-    if (!C.q_active || D.st[r].q_done) return;
-    if (threadIdx.x >= D.tile_n[t]) return;
-    const int i = D.tile_start[t] + threadIdx.x;
-    const RepDev &R = D.rep[r];
-    const int4 p = D.rec[i].p;
-    const int role = (p.w >> 8) & 0xff;
-    if (role == ROLE_FIXED) return;
-    if (D.prec == HD_FP64) {
-        const dbl4 f = D.f64[i];
-        qmove(D, R, C, r, i, p, role, f.x, f.y, f.z, D.v64);
-    } else {
-        const float4 f = D.f32[i];
-        qmove(D, R, C, r, i, p, role, (double)f.x, (double)f.y, (double)f.z, D.v32);
+    if (!C.q_active || D.st[r].q_done) return;        // the same for the whole CTA
+    double m = 0.0;
+    if (threadIdx.x < D.tile_n[t]) {
+        const int i = D.tile_start[t] + threadIdx.x;
+        const RepDev &R = D.rep[r];
+        const int4 p = D.rec[i].p;
+        const int role = (p.w >> 8) & 0xff;
+        dbl4 x;
+        if (role == ROLE_FIXED) {
+            if (D.q_ftol_stay > 0.0) x = D.x[i];
+        } else if (D.prec == HD_FP64) {
+            const dbl4 f = D.f64[i];
+            x = qmove(D, R, C, r, i, p, role, f.x, f.y, f.z, D.v64);
+        } else {
+            const float4 f = D.f32[i];
+            x = qmove(D, R, C, r, i, p, role, (double)f.x, (double)f.y, (double)f.z, D.v32);
+        }
+        if (D.q_ftol_stay > 0.0) m = disp2(x, D.xo[i]);      // every atom, as the transition test
     }
+    // displacement from r_O of the new iterate, for the next convergence test
+    if (D.q_ftol_stay > 0.0) gate_max(D, r, m);
 }
 
 // Largest displacement of the quenched copy from r_O per replica (minimum

@@ -89,7 +89,7 @@ def lib(build_if_missing: bool = False):
     L.hd_set_slider.argtypes = [vp, dp, C.c_int]
     L.hd_set_bias.argtypes = [vp, dp]
     L.hd_step.argtypes = [vp, C.c_int]
-    L.hd_quench.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
+    L.hd_quench.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                             C.POINTER(C.c_int32)]
     L.hd_read.argtypes = [vp, C.c_int, C.c_int, vp, sz]
     L.hd_info.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -132,10 +132,10 @@ def hd_step(ctx, n_steps):
     return lib().hd_step(ctx, int(n_steps))
 
 
-def hd_quench(ctx, method, ftol, max_iter, step_size, theta, adopt, flags):
+def hd_quench(ctx, method, ftol, max_iter, step_size, theta, ftol_stay, adopt, flags):
     fp = None if flags is None else flags.ctypes.data_as(C.POINTER(C.c_int32))
     return lib().hd_quench(ctx, int(method), float(ftol), int(max_iter), float(step_size), float(theta),
-                           int(adopt), fp)
+                           float(ftol_stay), int(adopt), fp)
 
 
 def hd_read(ctx, field, replica, dst):
@@ -284,20 +284,29 @@ class Batch:
     def set_bias(self, bias):
         self._ck(hd_set_bias(self.ctx, np.asarray(bias, dtype=np.float64).reshape(-1)))
 
-    def quench(self, method=1, ftol=1e-6, max_iter=20000, step_size=None, theta=0.5, adopt=0):
+    def quench(self, method=1, ftol=1e-6, max_iter=20000, step_size=None, theta=0.5, adopt=0, ftol_stay=0.0):
+        """hd_quench; returns the transition flags.  ftol_stay > ftol stops a
+        replica early once max|F| < ftol_stay with every atom within theta/2
+        of r_O."""
         if step_size is None:
             step_size = 0.002 if method == 0 else 0.005
         flags = np.zeros(self.n_rep, dtype=np.int32)
-        self._ck(hd_quench(self.ctx, method, ftol, max_iter, step_size, theta, adopt, flags))
+        self._ck(hd_quench(self.ctx, method, ftol, max_iter, step_size, theta, ftol_stay, adopt, flags))
         self.last_flags = flags
         return flags
 
     def qstats(self):
-        """Iterations (mean), largest final force, converged fraction and the
-        number of flagged replicas of the last quench."""
+        """Iterations (mean, max), largest final force of the replicas that
+        reached ftol, that stopped inside their basin and that did neither,
+        their fractions, and the number of flagged replicas of the last
+        quench."""
         ob = self.obs()
-        return {"iters": float(ob[:, 14].mean()), "iters_max": int(ob[:, 14].max()), "fmax": float(ob[:, 15].max()),
-                "converged": float(ob[:, 27].mean()),
+        cv = ob[:, 27]
+        return {"iters": float(ob[:, 14].mean()), "iters_max": int(ob[:, 14].max()),
+                "fmax": float(ob[cv == 1, 15].max()) if (cv == 1).any() else 0.0,
+                "fmax_stay": float(ob[cv == 2, 15].max()) if (cv == 2).any() else 0.0,
+                "fmax_unconverged": float(ob[cv == 0, 15].max()) if (cv == 0).any() else 0.0,
+                "converged": float((cv == 1).mean()), "stayed": float((cv == 2).mean()),
                 "flagged": int(getattr(self, "last_flags", np.zeros(1)).sum())}
 
     def _read(self, field, r, shape, dtype):

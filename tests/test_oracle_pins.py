@@ -375,6 +375,50 @@ def test_transition_flag(oracle_mod):
     assert flag2 and md2 > 0.9
 
 
+def _maxdisp(r, x):
+    """Largest minimum-image displacement of x from the replica's r_O (numpy)."""
+    d = x - r.pos_ref
+    for a in range(3):
+        if r.periodic[a]:
+            d[:, a] -= r.box[a] * np.rint(d[:, a] / r.box[a])
+    return float(np.sqrt((d * d).sum(axis=1)).max())
+
+
+def test_gated_quench_gives_the_full_quench_answer(oracle_mod):
+    """The quench that stops early in its basin (max|F| < ftol_stay with every
+    atom within keep = theta/2 of r_O) gives the transition test the answer of
+    the quench run to ftol: on a thermal state it stops sooner, within
+    theta - keep of the full quench's minimum, unflagged; on a forced slip the
+    early stop never applies and the two quenches are identical; with
+    ftol_stay = 0 it is the plain quench."""
+    base = small2d()
+    o = oracle_mod.OracleReplica(base, _params())
+    xstar, _, _ = o.quench(method=1, ftol=1e-8, max_iter=40000)
+    ref = base.copy()
+    ref.pos, ref.pos_ref = xstar.copy(), xstar.copy()
+    theta, keep = 0.5, 0.25
+    st = ref.copy()
+    st.pos = thermalise(ref, amp=0.03, seed=2).pos
+    o1 = oracle_mod.OracleReplica(st, _params())
+    xf, itf, ff = o1.quench(method=1, ftol=1e-6, max_iter=40000, step_size=0.005)
+    xg, itg, fg = o1.quench(method=1, ftol=1e-6, max_iter=40000, step_size=0.005, ftol_stay=1e-1, keep=keep)
+    assert ff < 1e-6 and 1e-6 <= fg < 1e-1
+    assert itg < itf
+    assert _maxdisp(st, xg) < keep and _maxdisp(st, xf) < theta
+    assert np.abs(xg - xf).max() < theta - keep
+    assert o1.transition(xg, theta)[0] == o1.transition(xf, theta)[0] == 0
+    x0, it0, f0 = o1.quench(method=1, ftol=1e-6, max_iter=40000, step_size=0.005, ftol_stay=0.0, keep=keep)
+    assert np.array_equal(x0, xf) and it0 == itf and f0 == ff
+    sl = ref.copy()
+    sl.pos = xstar.copy()
+    sl.pos[sl.type == 1, 0] += 2.0 ** (1.0 / 6.0)
+    o2 = oracle_mod.OracleReplica(sl, _params())
+    xf2, itf2, _ = o2.quench(method=1, ftol=1e-6, max_iter=40000, step_size=0.005)
+    xg2, itg2, _ = o2.quench(method=1, ftol=1e-6, max_iter=40000, step_size=0.005, ftol_stay=1e-1, keep=keep)
+    assert itg2 == itf2 and np.array_equal(xg2, xf2)
+    assert o2.transition(xg2, theta)[0] == 1 and _maxdisp(sl, xg2) > 0.9
+
+
 def test_diverging_quench_stops_cleanly(oracle_mod):
     """Steepest descent with a step beyond 2 / (largest curvature) runs away
     from a thermal configuration of the paper's 2-D model: the quench must

@@ -387,6 +387,50 @@ def test_quench_fire_3d_workload_model(hd, oracle_mod, workload_states, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_quench_in_basin_stop_matches_oracle(hd, oracle_mod, workload_states, prec):
+    """The quench's early stop inside the basin (max|F| < ftol_stay = 0.1 with
+    every atom within theta/2 of r_O) on the 14,272-atom 3-D model, in one
+    batch of two replicas: the thermal state stops there at the oracle's
+    iteration (FP64 form: the same iteration and positions; split form:
+    within 2 %), unflagged, and keeps its r_O; the same state held against an
+    r_O moved by 0.6 sigma never stops early, reaches ftol at the oracle's
+    iteration, is flagged, and adopts the quenched positions."""
+    st = workload_states[1]
+    far = st.copy()
+    far.pos_ref = st.pos_ref.copy()
+    far.pos_ref[:, 0] += 0.6
+    p = _params(prec=prec, bias_on=1)
+    ftol, stay, theta = 1e-2, 1e-1, 0.5
+    b = hd.Batch([st, far], p)
+    flags = b.quench(method=1, ftol=ftol, max_iter=20000, step_size=0.005, theta=theta, adopt=1, ftol_stay=stay)
+    res = []
+    for k, r in enumerate((st, far)):
+        o = oracle_mod.OracleReplica(r, p)
+        xq, it, fm = o.quench(method=1, ftol=ftol, max_iter=20000, step_size=0.005, ftol_stay=stay,
+                              keep=0.5 * theta)
+        res.append((o, xq, it, fm))
+    ob0, ob1 = b.obs(0), b.obs(1)
+    print("GPU iterations %d / %d (q_conv %g / %g); oracle %d / %d" % (
+        ob0["q_iter"], ob1["q_iter"], ob0["q_conv"], ob1["q_conv"], res[0][2], res[1][2]))
+    assert ob0["q_conv"] == 2.0 and ob1["q_conv"] == 1.0
+    assert list(flags) == [0, 1]
+    for k, (o, xq, it, fm) in enumerate(res):
+        ob = (ob0, ob1)[k]
+        assert flags[k] == int(o.transition(xq, theta)[0])
+        if prec == 0:
+            assert ob["q_iter"] == it
+            assert np.abs(b.qpos(k) - xq).max() < 1e-6
+        else:
+            assert abs(ob["q_iter"] - it) <= max(2, 0.02 * it)
+            assert np.abs(b.qpos(k) - xq).max() < 2e-3
+    assert res[0][3] >= ftol and res[0][3] < stay and res[1][3] < ftol
+    assert res[0][2] < res[1][2]
+    assert np.array_equal(b.ref(0), st.pos_ref)
+    assert np.array_equal(b.ref(1), b.qpos(1))
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_quench_sd_3d_workload_model(hd, oracle_mod, workload_states, prec):
     """Steepest descent on the 14,272-atom 3-D model: 300 iterations of the same
     step give the same positions (the iteration is contractive, so the FP32
