@@ -365,7 +365,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
     P.o_x = take(cur, N * sizeof(dbl4));
     P.o_xo = take(cur, N * sizeof(dbl4));
     P.o_xq = take(cur, N * sizeof(dbl4));
-    P.o_v = take(cur, N * sizeof(dbl4));     // velocities: FP64 (FP64 form) or FP32 (split form)
+    P.o_v = take(cur, N * sizeof(dbl4));     // velocities are FP64 in both forms
     P.o_vq = take(cur, N * v4);
     P.o_f = take(cur, N * v4);
     P.o_fq = take(cur, N * v4);
@@ -562,7 +562,6 @@ void fill_dev(hd_ctx *c) {
     D.x = at<dbl4>(b, P.o_x);
     D.xo = at<dbl4>(b, P.o_xo);
     D.v64 = at<dbl4>(b, P.o_v);
-    D.vf = at<float4>(b, P.o_v);          // the same block: FP64 form dbl4, split form float4
     D.po = at<int4>(b, P.o_po);
     if (P.prec == HD_FP64) {
         D.f64 = at<dbl4>(b, P.o_f);
@@ -810,7 +809,14 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     fill_dev(c);
     set_scalars(c->D, p);
     set_scalars(c->Q, p);
-    CK(nl_configure(c->D));
+    {
+        int nb = 0;
+        CK(nl_configure(c->D, &nb));
+        if (nb > 4) {
+            c->D.nl_grid = c->D.nl_grid / 4 * nb;    // nl_grid starts at 4 CTAs per SM
+            c->Q.nl_grid = c->D.nl_grid;
+        }
+    }
     c->D.any_nhc = 0;
     for (int r = 0; r < n_rep; ++r) c->D.any_nhc |= reps[r].nhc_len > 0;
     c->Q.any_nhc = c->D.any_nhc;
@@ -849,10 +855,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
             if (d.vel && d.role[i] != 0)
                 for (int a = 0; a < 3; ++a) v[a] = d.vel[3 * i + a];
             if (d.dim == 2) v[2] = 0.0;
-            if (P.prec == HD_FP64)
-                reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
-            else   // split form: FP32 velocities
-                reinterpret_cast<float4 *>(hv.data())[a0 + sl] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+            reinterpret_cast<dbl4 *>(hv.data())[a0 + sl] = make_dbl4(v[0], v[1], v[2], 0.0);
         }
     }
     if (upload_reps(c) != HD_OK) return c->status;
@@ -1162,7 +1165,7 @@ hd_status hd_read(hd_ctx *c, int field, int replica, void *h_dst, size_t bytes) 
         return vec3(c->Q.x, true, -1);
     case HD_FIELD_VEL:
         if (!need(n * 24)) break;
-        return vec3(c->ws + P.o_v, f64, -1);
+        return vec3(c->ws + P.o_v, true, -1);
     case HD_FIELD_FORCE:
         if (!need(n * 24)) break;
         return vec3(c->ws + P.o_f, f64, -1);

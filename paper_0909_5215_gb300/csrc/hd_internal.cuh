@@ -6,7 +6,7 @@
 //   atom's input index, which is also its Philox counter word):
 //     x      dbl4  FP64 position, w = LJ type           (never wrapped)
 //     xo     dbl4  basin minimum r_O
-//     v      dbl4 (FP64 form) | float4 (split form)    velocity
+//     v      dbl4     velocity (FP64 in both forms)
 //     po     int4 (split form)  fixed-point image of r_O
 //     f      dbl4 | float4   LJ force, w = per-atom energy (half of each pair)
 //     h      dbl4 | float4   H.(r - r_O), spring term included
@@ -154,7 +154,6 @@ struct Dev {
     dbl4 *x, *xo;
     dbl4 *v64, *f64, *h64, *dr64;
     float4 *v32, *f32, *h32;     // v32: the quench's FIRE velocities (split form)
-    float4 *vf;                  // split form: MD velocities in FP32
     int4 *po;                    // split form: fixed-point image of r_O (r - r_O = image difference)
     AtomRec *rec;                // fixed-point position + FP32 r - r_O
     int4 *pfixb;

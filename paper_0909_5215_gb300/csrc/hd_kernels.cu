@@ -146,8 +146,7 @@ __global__ void k_init(Dev D, const int *draw_vel) {
                 v2 = sd * z2;
             }
         }
-        if (D.prec == HD_FP64) D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
-        else D.vf[i] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+        D.v64[i] = make_dbl4(v0, v1, v2, 0.0);
     }
 }
 
@@ -1301,8 +1300,10 @@ __device__ __forceinline__ void dev_update64(const Dev &D, int t, int mode, cons
 }
 
 __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, const Scal &C) {
-    // split form: FP32 forces and velocities, FP64 positions; r - r_O from
-    // the fixed-point images of r and r_O
+    // split form: FP32 forces, FP64 velocities and positions (FP32 velocities
+    // would round every kick and thermostat step at 2^-24 of |v|, which after
+    // 100 steps puts sigma and the boosted clock beyond 1e-6 of FP64); r - r_O
+    // from the fixed-point images of r and r_O
     const int r = D.tile_rep[t];
     const RepDev &R = D.rep[r];
     const bool act = threadIdx.x < D.tile_n[t];
@@ -1313,68 +1314,65 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
     float kin = 0.f;
     if (role != ROLE_FIXED) {
         const double hh = 0.5 * D.dt;
-        const float hf = (float)hh;
-        float4 v = D.vf[i];
+        dbl4 v = D.v64[i];
         dbl4 x = D.x[i];
         if (role == ROLE_MOBILE) {
             const float4 F = D.f32[i], H = D.h32[i];
             const float4 dr = make_float4((float)ai.d.x * R.fx_lsb[0], (float)ai.d.y * R.fx_lsb[1],
                                           (float)ai.d.z * R.fx_lsb[2], 0.f);
             const float ca = (float)C.ca, cb = (float)C.cb;
-            float Fx = fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
-            float Fy = fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
-            float Fz = fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
-            if (C.ce != 0.0) {               // eigenvalue bias (Eq. 13, Eq. 15), from FP64 grad epsilon
+            double Fx = (double)fmaf(ca, H.x - F.x, fmaf(cb, dr.x, F.x));
+            double Fy = (double)fmaf(ca, H.y - F.y, fmaf(cb, dr.y, F.y));
+            double Fz = (double)fmaf(ca, H.z - F.z, fmaf(cb, dr.z, F.z));
+            if (C.ce != 0.0) {               // eigenvalue bias (Eq. 13, Eq. 15), FP64
                 const dbl4 g = D.eg[i];
-                Fx += (float)(C.ce * g.x);
-                Fy += (float)(C.ce * g.y);
-                Fz += (float)(C.ce * g.z);
+                Fx += C.ce * g.x;
+                Fy += C.ce * g.y;
+                Fz += C.ce * g.z;
             }
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
-            const float sc = (float)C.nhc_scale;
-            if (mode & MODE_KIN) kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+            if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             if (mode & MODE_SCALE) {
                 if (chain) {
-                    v.x *= sc;
-                    v.y *= sc;
-                    v.z *= sc;
+                    v.x *= C.nhc_scale;
+                    v.y *= C.nhc_scale;
+                    v.z *= C.nhc_scale;
                 }
-                kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             }
             if (mode & MODE_CLOSE) {
-                v.x = fmaf(hf, Fx, v.x);
-                v.y = fmaf(hf, Fy, v.y);
-                if (three) v.z = fmaf(hf, Fz, v.z);
-                kin = 0.5f * (v.x * v.x + v.y * v.y + v.z * v.z);
+                v.x += hh * Fx;
+                v.y += hh * Fy;
+                if (three) v.z += hh * Fz;
+                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
             }
             if (mode & MODE_OPEN) {
                 if (chain && (mode & MODE_NHC)) {
-                    v.x *= sc;
-                    v.y *= sc;
-                    v.z *= sc;
+                    v.x *= C.nhc_scale;
+                    v.y *= C.nhc_scale;
+                    v.z *= C.nhc_scale;
                 }
-                v.x = fmaf(hf, Fx, v.x);
-                v.y = fmaf(hf, Fy, v.y);
-                if (three) v.z = fmaf(hf, Fz, v.z);
-                const float ax = v.x, ay = v.y, az = v.z;
+                v.x += hh * Fx;
+                v.y += hh * Fy;
+                if (three) v.z += hh * Fz;
+                const double ax = v.x, ay = v.y, az = v.z;
                 if (!chain) {
                     float n0, n1, n2, n3;
                     normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 0), n0, n1);
-                    v.x = fmaf(R.c_ouf, v.x, R.s_ouf * n0);
-                    v.y = fmaf(R.c_ouf, v.y, R.s_ouf * n1);
+                    v.x = R.c_ou * v.x + R.s_ou * (double)n0;
+                    v.y = R.c_ou * v.y + R.s_ou * (double)n1;
                     if (three) {
                         normals32(philox_draw(D, C.step_cur, D.orig[i], R.rep_id, 1), n2, n3);
-                        v.z = fmaf(R.c_ouf, v.z, R.s_ouf * n2);
+                        v.z = R.c_ou * v.z + R.s_ou * (double)n2;
                     }
                 }
-                // the two half drifts A of BAOAB, in FP64
-                x.x += hh * (double)(ax + v.x);
-                x.y += hh * (double)(ay + v.y);
-                if (three) x.z += hh * (double)(az + v.z);
+                x.x += hh * (ax + v.x);
+                x.y += hh * (ay + v.y);
+                if (three) x.z += hh * (az + v.z);
             }
         } else {
-            if (mode & MODE_CLOSE) v = make_float4((float)C.vb_mid[0], (float)C.vb_mid[1], (float)C.vb_mid[2], 0.f);
+            if (mode & MODE_CLOSE) v = make_dbl4(C.vb_mid[0], C.vb_mid[1], C.vb_mid[2], 0.0);
             if (mode & MODE_OPEN) {
                 x.x += hh * C.vb_new[0];
                 x.y += hh * C.vb_new[1];
@@ -1382,10 +1380,10 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
                 x.x += hh * C.vb_new[0];
                 x.y += hh * C.vb_new[1];
                 x.z += hh * C.vb_new[2];
-                v = make_float4((float)C.vb_new[0], (float)C.vb_new[1], (float)C.vb_new[2], 0.f);
+                v = make_dbl4(C.vb_new[0], C.vb_new[1], C.vb_new[2], 0.0);
             }
         }
-        D.vf[i] = v;
+        D.v64[i] = v;
         if (mode & MODE_OPEN) {
             D.x[i] = x;
             post_move32(D, R, r, i, x, p);
@@ -1830,9 +1828,13 @@ static size_t persist_smem_bytes(const Dev &D) {
     const size_t a = nl_smem_bytes(D), b = pair_smem_bytes_for(D.block);
     return a > b ? a : b;
 }
-cudaError_t nl_configure(const Dev &D) {
+cudaError_t nl_configure(const Dev &D, int *nl_blocks_per_sm) {
     const int bytes = (int)nl_smem_bytes(D), pbytes = (int)persist_smem_bytes(D);
     cudaError_t e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    // the row builder is latency-bound: launch as many CTAs as fit
+    *nl_blocks_per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(nl_blocks_per_sm, k_nlist, 128, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_persist<HD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
     if (e != cudaSuccess) return e;

@@ -19,11 +19,12 @@ void launch_obs(const Dev &D, cudaStream_t s);
 void launch_nhc(const Dev &D, int mode, cudaStream_t s);          // the chain between two kicks, per replica
 void launch_eig(const Dev &D, cudaStream_t s);                    // epsilon (Lanczos) and grad epsilon (hd_eig.cu)
 void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s);
-void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 6 kernels
+void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 8 kernels
 void launch_qdisp(const Dev &Q, cudaStream_t s);
 void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s);
 size_t nl_smem_bytes(const Dev &D);                               // dynamic shared memory of the list build
-cudaError_t nl_configure(const Dev &D);                           // allow that much on the kernels that build lists
+// allow that much on the kernels that build lists; *nl_blocks_per_sm: resident row-build CTAs per SM
+cudaError_t nl_configure(const Dev &D, int *nl_blocks_per_sm);
 int persist_blocks_per_sm(const Dev &D);                          // resident CTAs of the persistent kernel
 cudaError_t launch_persist(const Dev &D, int grid, int nsteps, cudaStream_t s);  // cooperative, n steps
 
