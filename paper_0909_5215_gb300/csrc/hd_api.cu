@@ -201,6 +201,7 @@ bool make_plan(const hd_replica_desc *reps, int n_rep, const hd_params *p, Plan 
             if (R.nc[a] >= 1024) { why = "replica " + std::to_string(r) + ": more than 1023 cells along an axis"; return false; }
         }
         for (int a = 0; a < 3; ++a) {
+            R.fx_add[a] = 6755399441055744.0 - R.fx_origin[a] * R.fx_scale[a];   // 1.5 2^52 - origin scale
             const double u = R.fx_scale[a] != 0.0 ? 1.0 / R.fx_scale[a] : 0.0;
             R.lsb_rel[a] = R.fx_lsb[a] != 0.f ? (float)((u - (double)R.fx_lsb[a]) / (double)R.fx_lsb[a]) : 0.f;
         }

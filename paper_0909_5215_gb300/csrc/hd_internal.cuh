@@ -79,8 +79,11 @@ struct RepDev {
     double dvmax, sig_lo, sig_hi;
     double eps[2][2], sig2[2][2], shift[2][2];
     float epsf[2][2], sig2f[2][2], shiftf[2][2];
-    // fine fixed point of the pair sweep: q = rint((x - origin) * scale) mod 2^32
-    double fx_scale[3], fx_origin[3];
+    // fine fixed point of the pair sweep: q = rint(x * scale - origin * scale)
+    // mod 2^32, taken as the low word of fma(x, scale, fx_add) with
+    // fx_add = 1.5 2^52 - origin * scale (a common offset of at most half a
+    // unit per axis, which every difference of images cancels)
+    double fx_scale[3], fx_origin[3], fx_add[3];
     float fx_lsb[3];
     int fine_shift;              // periodic axes count 2^(32 + fine_shift) units per L
     double bin_scale[3];         // periodic axes: 2^32 / L, the exact integer cell map
@@ -247,16 +250,14 @@ __device__ __forceinline__ void normals32(uint4 w, float &n0, float &n1) {
     n1 = rad * fmaf(c, da, s);
 }
 
-// rint(q) mod 2^32 for |q| < 2^51: adding 1.5 2^52 leaves rint(q) (rounded to
-// nearest even, like rint) in the low bits of the sum's significand, and
-// 1.5 2^52 is a multiple of 2^32, so the sum's low word is the residue.  One
-// FP64 add instead of a 64-bit float-to-integer conversion.
-__device__ __forceinline__ int rint_low32(double q) { return __double2loint(q + 6755399441055744.0); }
-
-// Fixed-point image of one coordinate.
+// Fixed-point image of one coordinate in one FP64 instruction: for
+// |x scale - origin scale| < 2^51 the fused x * scale + fx_add lies in
+// [2^52, 2^53), where doubles are the integers, so it is 1.5 2^52 plus the
+// rounded (nearest even) image, and 1.5 2^52 is a multiple of 2^32: the low
+// word is the image mod 2^32.  An axis without a grid has scale 0 and
+// fx_add = 1.5 2^52, so its image is 0.
 __device__ __forceinline__ int fix_coord(const RepDev &R, int a, double x) {
-    if (R.fx_scale[a] == 0.0) return 0;
-    return rint_low32((x - R.fx_origin[a]) * R.fx_scale[a]);
+    return __double2loint(fma(x, R.fx_scale[a], R.fx_add[a]));
 }
 
 __device__ __forceinline__ int4 fix_pos(const RepDev &R, dbl4 x, int w) {

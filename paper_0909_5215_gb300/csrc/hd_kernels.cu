@@ -1311,6 +1311,12 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
     const AtomRec ai = D.rec[i];
     const int4 p = ai.p;
     const int role = act ? ((p.w >> 8) & 0xff) : ROLE_FIXED;
+    // the closing half kick of one step and the opening one of the next see
+    // the same force: between steps of one call a Langevin replica takes one
+    // full kick in FP64 (this GPU's FP64 rate is a small fraction of its FP32
+    // rate).  The kinetic energy at the half step is an observable there, not
+    // an input, and is summed only on the closing half of a call's last step.
+    const bool fused = R.nhc_len == 0 && (mode & MODE_CLOSE) && (mode & MODE_OPEN);
     float kin = 0.f;
     if (role != ROLE_FIXED) {
         const double hh = 0.5 * D.dt;
@@ -1332,30 +1338,38 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
             }
             const bool three = R.dim == 3;
             const bool chain = R.nhc_len > 0;
-            if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
-            if (mode & MODE_SCALE) {
-                if (chain) {
-                    v.x *= C.nhc_scale;
-                    v.y *= C.nhc_scale;
-                    v.z *= C.nhc_scale;
+            if (fused) {
+                v.x = fma(D.dt, Fx, v.x);
+                v.y = fma(D.dt, Fy, v.y);
+                if (three) v.z = fma(D.dt, Fz, v.z);
+            } else {
+                if (mode & MODE_KIN) kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+                if (mode & MODE_SCALE) {
+                    if (chain) {
+                        v.x *= C.nhc_scale;
+                        v.y *= C.nhc_scale;
+                        v.z *= C.nhc_scale;
+                    }
+                    kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
                 }
-                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
-            }
-            if (mode & MODE_CLOSE) {
-                v.x += hh * Fx;
-                v.y += hh * Fy;
-                if (three) v.z += hh * Fz;
-                kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+                if (mode & MODE_CLOSE) {
+                    v.x += hh * Fx;
+                    v.y += hh * Fy;
+                    if (three) v.z += hh * Fz;
+                    kin = (float)(0.5 * (v.x * v.x + v.y * v.y + v.z * v.z));
+                }
+                if (mode & MODE_OPEN) {
+                    if (chain && (mode & MODE_NHC)) {
+                        v.x *= C.nhc_scale;
+                        v.y *= C.nhc_scale;
+                        v.z *= C.nhc_scale;
+                    }
+                    v.x += hh * Fx;
+                    v.y += hh * Fy;
+                    if (three) v.z += hh * Fz;
+                }
             }
             if (mode & MODE_OPEN) {
-                if (chain && (mode & MODE_NHC)) {
-                    v.x *= C.nhc_scale;
-                    v.y *= C.nhc_scale;
-                    v.z *= C.nhc_scale;
-                }
-                v.x += hh * Fx;
-                v.y += hh * Fy;
-                if (three) v.z += hh * Fz;
                 const double ax = v.x, ay = v.y, az = v.z;
                 if (!chain) {
                     float n0, n1, n2, n3;
@@ -1389,7 +1403,7 @@ __device__ __forceinline__ void dev_update32(const Dev &D, int t, int mode, cons
             post_move32(D, R, r, i, x, p);
         }
     }
-    if (mode & (MODE_CLOSE | MODE_KIN | MODE_SCALE)) {
+    if ((mode & (MODE_CLOSE | MODE_KIN | MODE_SCALE)) && !fused) {
         double v1[1] = {(double)warp_sum(kin)};
         if ((threadIdx.x & 31) != 0) v1[0] = 0.0;
         cta_reduce<1>(v1, D.kpart + t, -1);
@@ -1602,6 +1616,41 @@ __device__ __forceinline__ dbl4 qmove(const Dev &D, const RepDev &R, const Scal 
     return x;
 }
 
+// The split form's FIRE move in FP32 (its velocities are FP32 and its forces
+// FP32 already): only the position, kept in FP64, takes FP64 adds.
+__device__ __forceinline__ dbl4 qmove32(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
+                                        float fx, float fy, float fz) {
+    if (D.q_method == 0) return qmove(D, R, C, r, i, p, role, (double)fx, (double)fy, (double)fz, D.v32);
+    dbl4 x = D.x[i];
+    const bool three = R.dim == 3;
+    const float dt = (float)C.q_dt;
+    if (role == ROLE_MOBILE) {
+        float4 v = D.v32[i];
+        if (C.q_zero) {
+            v.x = v.y = v.z = 0.f;
+        } else {
+            const float keep = (float)(1.0 - C.q_alpha), mix = (float)C.q_mix;
+            v.x = fmaf(keep, v.x, mix * fx);
+            v.y = fmaf(keep, v.y, mix * fy);
+            v.z = fmaf(keep, v.z, mix * fz);
+        }
+        v.x = fmaf(dt, fx, v.x);
+        v.y = fmaf(dt, fy, v.y);
+        v.z = three ? fmaf(dt, fz, v.z) : 0.f;
+        x.x += (double)(dt * v.x);
+        x.y += (double)(dt * v.y);
+        if (three) x.z += (double)(dt * v.z);
+        D.v32[i] = v;
+    } else {
+        x.x += C.q_dt * C.q_vb[0];
+        x.y += C.q_dt * C.q_vb[1];
+        if (three) x.z += C.q_dt * C.q_vb[2];
+    }
+    D.x[i] = x;
+    post_move(D, R, r, i, x, p);
+    return x;
+}
+
 __global__ void __launch_bounds__(256) k_qupdate(Dev D) {
     const int t = blockIdx.x, r = D.tile_rep[t];
     const Scal &C = D.sc[r];
@@ -1620,7 +1669,7 @@ __global__ void __launch_bounds__(256) k_qupdate(Dev D) {
             x = qmove(D, R, C, r, i, p, role, f.x, f.y, f.z, D.v64);
         } else {
             const float4 f = D.f32[i];
-            x = qmove(D, R, C, r, i, p, role, (double)f.x, (double)f.y, (double)f.z, D.v32);
+            x = qmove32(D, R, C, r, i, p, role, f.x, f.y, f.z);
         }
         if (D.q_ftol_stay > 0.0) m = disp2(x, D.xo[i]);      // every atom, as the transition test
     }
