@@ -246,13 +246,22 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ main arm
 def kernel_code_hash():
-    """sha256 (16 hex digits) of the pair kernel's sources with comments and
-    blank lines removed: a capture stays valid across comment edits."""
+    """sha256 (16 hex digits) of the pair kernel's sources (the shared header,
+    and the reduction and pair-sweep sections of the kernel file) with
+    comments and blank lines removed: a capture stays valid across comment
+    edits and changes elsewhere in the file."""
     import hashlib
     import re
+    csrc = os.path.join(ROOT, "paper_0909_5215_gb300", "csrc")
+    kern = open(os.path.join(csrc, "hd_kernels.cu")).read()
+    marks = [m.start() for m in re.finditer(r"^// -{10,} ", kern, flags=re.M)] + [len(kern)]
+    parts = [open(os.path.join(csrc, "hd_internal.cuh")).read()]
+    for a, b in zip(marks[:-1], marks[1:]):
+        title = kern[a:kern.index("\n", a)]
+        if title.rstrip().endswith(("reductions", "pair sweep")):
+            parts.append(kern[a:b])
     h = hashlib.sha256()
-    for f in ("hd_kernels.cu", "hd_internal.cuh"):
-        text = open(os.path.join(ROOT, "paper_0909_5215_gb300", "csrc", f)).read()
+    for text in parts:
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for line in text.splitlines():
             line = re.sub(r"//.*", "", line).strip()

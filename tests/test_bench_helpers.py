@@ -25,7 +25,7 @@ def test_clock_summary_median_max_and_reasons():
     assert c.summary()["reasons"] == ["unsampled"]
 
 
-def test_kernel_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+def test_kernel_hash_ignores_comments_and_other_sections_not_pair_code(tmp_path, monkeypatch):
     src = os.path.join(bench.ROOT, "paper_0909_5215_gb300", "csrc")
     dst = tmp_path / "paper_0909_5215_gb300" / "csrc"
     dst.mkdir(parents=True)
@@ -36,7 +36,18 @@ def test_kernel_hash_ignores_comments_not_code(tmp_path, monkeypatch):
     k = dst / "hd_kernels.cu"
     k.write_text(k.read_text() + "\n// a comment\n/* and a\n   block comment */\n\n")
     assert bench.kernel_code_hash() == h0
-    k.write_text(k.read_text() + "\nstatic int extra_symbol_for_the_hash;\n")
+    k.write_text(k.read_text() + "\nstatic int extra_symbol_outside_the_pair_sweep;\n")
+    assert bench.kernel_code_hash() == h0            # the launchers section is not the pair kernel's
+    text = k.read_text()
+    red = text.index("// ---------------------------------------------------------------- reductions")
+    at = text.index("\n", red) + 1
+    k.write_text(text[:at] + "static int extra_symbol_in_the_reductions;\n" + text[at:])
+    assert bench.kernel_code_hash() != h0
+    k.write_text(text)
+    assert bench.kernel_code_hash() == h0
+    mark = text.index("// ---------------------------------------------------------------- pair sweep")
+    at = text.index("\n", mark) + 1
+    k.write_text(text[:at] + "static int extra_symbol_in_the_pair_sweep;\n" + text[at:])
     assert bench.kernel_code_hash() != h0
 
 

@@ -332,13 +332,17 @@ def workload_states(oracle_mod):
 
 
 def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_states):
-    """The split form's bound: DeltaV and the t_h increment within 1e-6
-    (relative) of the FP64 oracle after 100 steps from one state.  The band of
-    Eq. 14 is the 10%-90% range of sigma over an unbiased 100-step oracle
-    pre-run from the same state, as in the full-size tests, so that DeltaV
-    moves through the band.  (A band of +-15% around the starting slope makes
-    DeltaV's relative error about 20 times sigma's on the 3-D model: there
-    the 4.5e-8 of sigma became 1.1e-6 in the t_h increment.)"""
+    """The split form's bound after 100 steps from one state: sigma within
+    1e-6 (relative) of the FP64 oracle, and DeltaV and the t_h increment
+    within what a relative error of 1e-6 in sigma and DeltaV makes of them
+    through Eq. 14 and Eq. 3: |dDeltaV| <= 1e-6 (|sigma DeltaV'| + |DeltaV|),
+    |dt_h| <= 1e-6 sum_n dt exp(beta DeltaV_n) (1 + beta |sigma_n DeltaV'_n|).
+    Inside the band the bias multiplies sigma's relative error by
+    beta |sigma DeltaV'|, 19 on average (55 at most) on the 421-atom 2-D
+    model with this band, so a flat 1e-6 on t_h would ask sigma for 5e-8.
+    The band of Eq. 14 is the 10%-90% range of sigma over an unbiased
+    100-step oracle pre-run from the same state, as in the full-size tests,
+    so that DeltaV moves through the band."""
     from bandtools import run_band_prerun
     states = [s.copy() for s in workload_states]
     run_band_prerun(oracle_mod, states, _params(prec=1, bias_on=1), [0, 1], steps=100, draw=None)
@@ -349,17 +353,23 @@ def test_split_dv_and_hypertime_on_workload_models(hd, oracle_mod, workload_stat
         assert abs(ob["dV"] - o.s.dV) <= 1e-6 * (abs(o.s.sigma * o.s.dVp) + abs(o.s.dV)) + 1e-12
     th0 = [o.s.t_h for o in ors]
     b.step(100)
-    report = []
+    report, th_tol = [], []
     for k, o in enumerate(ors):
-        o.run(100)
+        kT, tol = workload_states[k].kT, 0.0
+        for _ in range(100):
+            tol += 0.005 * np.exp(o.s.dV / kT) * (1.0 + abs(o.s.sigma * o.s.dVp) / kT)
+            o.run(1)
+        th_tol.append(1e-6 * tol)
         ob = b.obs(k)
-        report.append("replica %d (dim %d): rel err of the t_h increment %.2e, |ddV| %.2e (dV %.3e), sigma %.2e" % (
-            k, workload_states[k].dim, abs((ob["t_h"] - th0[k]) / (o.s.t_h - th0[k]) - 1),
-            abs(ob["dV"] - o.s.dV), o.s.dV, abs(ob["sigma"] / o.s.sigma - 1)))
+        report.append("replica %d (dim %d): t_h increment off by %.2e (rel %.2e; bound %.2e), |ddV| %.2e "
+                      "(dV %.3e), sigma %.2e" % (
+                          k, workload_states[k].dim, abs(ob["t_h"] - o.s.t_h),
+                          abs((ob["t_h"] - th0[k]) / (o.s.t_h - th0[k]) - 1), th_tol[k],
+                          abs(ob["dV"] - o.s.dV), o.s.dV, abs(ob["sigma"] / o.s.sigma - 1)))
     print("\n".join(report))
     for k, o in enumerate(ors):
         ob = b.obs(k)
-        assert ob["t_h"] - th0[k] == pytest.approx(o.s.t_h - th0[k], rel=1e-6), report
+        assert abs((ob["t_h"] - th0[k]) - (o.s.t_h - th0[k])) <= th_tol[k], report
         assert abs(ob["dV"] - o.s.dV) <= 1e-6 * (abs(o.s.sigma * o.s.dVp) + abs(o.s.dV)) + 1e-12, report
         assert ob["sigma"] == pytest.approx(o.s.sigma, rel=1e-6), report
         assert o.s.t_h - th0[k] > 1.0001 * 100 * 0.005, "the bias never acted"
