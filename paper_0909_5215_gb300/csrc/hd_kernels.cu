@@ -1171,7 +1171,7 @@ __global__ void k_nhc(Dev D, int mode) {
 //   CLOSE: v += dt/2 F_tot                      (end of the previous step)
 //   OPEN:  v += dt/2 F_tot; x += dt/2 v; v = c v + s xi; x += dt/2 v
 // Mobile atoms only; rigid atoms follow the body velocity; fixed atoms stay.
-__device__ __forceinline__ void post_move(const Dev &D, const RepDev &R, int r, int i, dbl4 x, int4 p) {
+__device__ __forceinline__ int4 post_move(const Dev &D, const RepDev &R, int r, int i, dbl4 x, int4 p) {
     const int4 q = fix_pos(R, x, p.w);
     D.rec[i].p = q;
     const int4 b = D.pfixb[i];
@@ -1182,6 +1182,7 @@ __device__ __forceinline__ void post_move(const Dev &D, const RepDev &R, int r, 
     const double zv = R.vert == 2 ? x.z : x.y;
     if (!(fabs(zv - R.fx_origin[R.vert]) < R.open_lim) || !isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z))
         set_err(D, HD_ERR_NUMERIC, i, r);
+    return q;
 }
 
 // Split form: the new fixed-point image and r - r_O as the difference of
@@ -1426,6 +1427,18 @@ __device__ __forceinline__ double disp2(dbl4 a, dbl4 b) {
     return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
 }
 
+// Split form: |x - r_O|^2 in FP32 from the difference of the fixed-point
+// images of x and r_O (exact integers; no FP64 instruction).  A difference
+// beyond 3/4 of the image range reads as far.  The early stop compares it
+// with (theta/2)^2, where FP32 rounding can only matter within ~1e-7 of it.
+__device__ __forceinline__ float disp2_img(const RepDev &R, int4 q, int4 po) {
+    const int4 d = img_diff(q, po);
+    const int lim = 3 << 29;
+    if (abs(d.x) > lim || abs(d.y) > lim || abs(d.z) > lim) return 3.0e38f;
+    const float dx = (float)d.x * R.fx_lsb[0], dy = (float)d.y * R.fx_lsb[1], dz = (float)d.z * R.fx_lsb[2];
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
 // Largest m over the CTA into qgate[r] (non-negative doubles order as their
 // bit patterns).  Every thread of the CTA calls it.
 __device__ __forceinline__ void gate_max(const Dev &D, int r, double m) {
@@ -1438,6 +1451,20 @@ __device__ __forceinline__ void gate_max(const Dev &D, int r, double m) {
         double a = sm[0];
         for (int k = 1; k < nw; ++k) a = fmax(a, sm[k]);
         atomicMax(D.qgate + r, (unsigned long long)__double_as_longlong(a));
+    }
+}
+// The same over FP32 values, converted once per CTA.
+__device__ __forceinline__ void gate_max_f(const Dev &D, int r, float m) {
+    __shared__ float smf[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (lane == 0) smf[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = smf[0];
+        for (int k = 1; k < nw; ++k) a = fmaxf(a, smf[k]);
+        atomicMax(D.qgate + r, (unsigned long long)__double_as_longlong((double)a));
     }
 }
 
@@ -1459,16 +1486,24 @@ __global__ void k_qinit(Dev Q, Dev M) {
         Q.rebuild[r] = 2;
     }
     double m = 0.0;
+    float mf = 0.f;
     if (threadIdx.x < Q.tile_n[t]) {
         const int i = Q.tile_start[t] + threadIdx.x;
         const dbl4 x = M.x[i];
+        const int4 p = M.rec[i].p;
         Q.x[i] = x;
-        Q.rec[i].p = M.rec[i].p;
+        Q.rec[i].p = p;
         if (Q.prec == HD_FP64) Q.v64[i] = make_dbl4(0, 0, 0, 0);
         else Q.v32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (Q.q_ftol_stay > 0.0) m = disp2(x, Q.xo[i]);
+        if (Q.q_ftol_stay > 0.0) {
+            if (Q.prec == HD_FP64) m = disp2(x, Q.xo[i]);
+            else mf = disp2_img(Q.rep[r], p, Q.po[i]);
+        }
     }
-    if (Q.q_ftol_stay > 0.0) gate_max(Q, r, m);
+    if (Q.q_ftol_stay > 0.0) {
+        if (Q.prec == HD_FP64) gate_max(Q, r, m);
+        else gate_max_f(Q, r, mf);
+    }
 }
 
 // Convergence test and FIRE bookkeeping (reading of Bitzek et al. 2006: mix
@@ -1569,7 +1604,7 @@ __global__ void k_qscalar(Dev D, int max_iter) {
 // or zero, the velocity, then a semi-implicit Euler step.
 template <typename V4>
 __device__ __forceinline__ dbl4 qmove(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
-                                      double fx, double fy, double fz, V4 *vq) {
+                                      double fx, double fy, double fz, V4 *vq, int4 *img) {
     dbl4 x = D.x[i];
     const int dim = R.dim;
     if (D.q_method == 0) {
@@ -1612,15 +1647,19 @@ __device__ __forceinline__ dbl4 qmove(const Dev &D, const RepDev &R, const Scal 
         }
     }
     D.x[i] = x;
-    post_move(D, R, r, i, x, p);
+    *img = post_move(D, R, r, i, x, p);
     return x;
 }
 
 // The split form's FIRE move in FP32 (its velocities are FP32 and its forces
 // FP32 already): only the position, kept in FP64, takes FP64 adds.
-__device__ __forceinline__ dbl4 qmove32(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
+__device__ __forceinline__ int4 qmove32(const Dev &D, const RepDev &R, const Scal &C, int r, int i, int4 p, int role,
                                         float fx, float fy, float fz) {
-    if (D.q_method == 0) return qmove(D, R, C, r, i, p, role, (double)fx, (double)fy, (double)fz, D.v32);
+    if (D.q_method == 0) {
+        int4 q;
+        qmove(D, R, C, r, i, p, role, (double)fx, (double)fy, (double)fz, D.v32, &q);
+        return q;
+    }
     dbl4 x = D.x[i];
     const bool three = R.dim == 3;
     const float dt = (float)C.q_dt;
@@ -1647,34 +1686,46 @@ __device__ __forceinline__ dbl4 qmove32(const Dev &D, const RepDev &R, const Sca
         if (three) x.z += C.q_dt * C.q_vb[2];
     }
     D.x[i] = x;
-    post_move(D, R, r, i, x, p);
-    return x;
+    return post_move(D, R, r, i, x, p);
 }
 
 __global__ void __launch_bounds__(256) k_qupdate(Dev D) {
     const int t = blockIdx.x, r = D.tile_rep[t];
     const Scal &C = D.sc[r];
     if (!C.q_active || D.st[r].q_done) return;        // the same for the whole CTA
+    // displacement from r_O of the new iterate (every atom, as in the
+    // transition test), for the next convergence test
+    const bool gate = D.q_ftol_stay > 0.0;
     double m = 0.0;
+    float mf = 0.f;
     if (threadIdx.x < D.tile_n[t]) {
         const int i = D.tile_start[t] + threadIdx.x;
         const RepDev &R = D.rep[r];
         const int4 p = D.rec[i].p;
         const int role = (p.w >> 8) & 0xff;
-        dbl4 x;
-        if (role == ROLE_FIXED) {
-            if (D.q_ftol_stay > 0.0) x = D.x[i];
-        } else if (D.prec == HD_FP64) {
-            const dbl4 f = D.f64[i];
-            x = qmove(D, R, C, r, i, p, role, f.x, f.y, f.z, D.v64);
+        if (D.prec == HD_FP64) {
+            dbl4 x;
+            int4 q;
+            if (role == ROLE_FIXED) {
+                if (gate) x = D.x[i];
+            } else {
+                const dbl4 f = D.f64[i];
+                x = qmove(D, R, C, r, i, p, role, f.x, f.y, f.z, D.v64, &q);
+            }
+            if (gate) m = disp2(x, D.xo[i]);
         } else {
-            const float4 f = D.f32[i];
-            x = qmove32(D, R, C, r, i, p, role, f.x, f.y, f.z);
+            int4 q = p;
+            if (role != ROLE_FIXED) {
+                const float4 f = D.f32[i];
+                q = qmove32(D, R, C, r, i, p, role, f.x, f.y, f.z);
+            }
+            if (gate) mf = disp2_img(R, q, D.po[i]);
         }
-        if (D.q_ftol_stay > 0.0) m = disp2(x, D.xo[i]);      // every atom, as the transition test
     }
-    // displacement from r_O of the new iterate, for the next convergence test
-    if (D.q_ftol_stay > 0.0) gate_max(D, r, m);
+    if (gate) {
+        if (D.prec == HD_FP64) gate_max(D, r, m);
+        else gate_max_f(D, r, mf);
+    }
 }
 
 // Largest displacement of the quenched copy from r_O per replica (minimum

@@ -457,7 +457,13 @@ def test_quench_sd_3d_workload_model(hd, oracle_mod, workload_states, prec):
     _, it1, fm1 = o.quench(method=0, ftol=1e-12, max_iter=301, step_size=0.002)
     ob = b.obs(0)
     assert ob["q_iter"] == it == 300 and it1 == 301 and ob["q_conv"] == 0.0
-    assert ob["q_fmax"] == pytest.approx(fm1, rel=1e-9 if prec == 0 else 1e-3)
+    # split form: the largest force is the rigid body's, a sum of 88 FP32 forces
+    # that nearly cancel against the spring and the load; its FP32 noise is the
+    # ~5e-4 floor of the split-form quench
+    if prec == 0:
+        assert ob["q_fmax"] == pytest.approx(fm1, rel=1e-9)
+    else:
+        assert abs(ob["q_fmax"] - fm1) < 5e-4
     assert np.abs(b.qpos(0) - xq).max() < (1e-9 if prec == 0 else 1e-5)
     # an unconverged quench never becomes r_O
     b.quench(method=0, ftol=1e-12, max_iter=50, step_size=0.002, theta=0.0, adopt=2)
