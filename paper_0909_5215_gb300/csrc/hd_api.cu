@@ -813,7 +813,7 @@ hd_status hd_create(const hd_replica_desc *reps, int n_rep, const hd_params *p, 
     {
         int nb = 0;
         CK(nl_configure(c->D, &nb));
-        if (nb > 4) {
+        if (nb > 0) {
             c->D.nl_grid = c->D.nl_grid / 4 * nb;    // nl_grid starts at 4 CTAs per SM
             c->Q.nl_grid = c->D.nl_grid;
         }

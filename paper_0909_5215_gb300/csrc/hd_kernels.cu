@@ -288,6 +288,8 @@ __global__ void __launch_bounds__(128) k_cellsort(Dev D) {
 // lists (sorted by k_cellsort); reads return each row ascending in j.
 // ballot masks per warp of the list build: three per 32 staged candidates
 __host__ __device__ inline int nl_mask_words(const Dev &D) { return 3 * ((27 * D.cell_cap + 31) / 32); }
+// Row-build CTA: 8 warps share one staged stencil (the cell's atoms split among them).
+constexpr int NL_THREADS = 256;
 
 struct NlSmem {
     int nst, tot, kc;
@@ -459,7 +461,7 @@ __device__ __forceinline__ void nl_smem_carve(const Dev &D, char *base, int4 *&s
     smask = reinterpret_cast<unsigned *>(base + (size_t)27 * D.cell_cap * sizeof(int4));
 }
 
-__global__ void __launch_bounds__(128) k_nlist(Dev D) {
+__global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev D) {
     extern __shared__ __align__(16) char nl_smem[];
     __shared__ NlSmem M;
     int4 *sp;
@@ -1920,21 +1922,21 @@ static inline int nthr(const Dev &D) { return D.block; }
 // Dynamic shared memory of the list build: positions, indices and classes
 // of up to 27 cells of cell_cap candidates (classes: one byte per candidate
 // for each of the warps of a 128-thread CTA).
-size_t nl_smem_bytes(const Dev &D) {
-    return 27 * (size_t)D.cell_cap * sizeof(int4) + 4 * (size_t)nl_mask_words(D) * sizeof(unsigned);
+size_t nl_smem_bytes(const Dev &D, int nwarps) {
+    return 27 * (size_t)D.cell_cap * sizeof(int4) + (size_t)nwarps * nl_mask_words(D) * sizeof(unsigned);
 }
 // the persistent kernel runs the list build and the pair sweep in one launch
 static size_t persist_smem_bytes(const Dev &D) {
-    const size_t a = nl_smem_bytes(D), b = pair_smem_bytes_for(D.block);
+    const size_t a = nl_smem_bytes(D, (D.block + 31) / 32), b = pair_smem_bytes_for(D.block);
     return a > b ? a : b;
 }
 cudaError_t nl_configure(const Dev &D, int *nl_blocks_per_sm) {
-    const int bytes = (int)nl_smem_bytes(D), pbytes = (int)persist_smem_bytes(D);
+    const int bytes = (int)nl_smem_bytes(D, NL_THREADS / 32), pbytes = (int)persist_smem_bytes(D);
     cudaError_t e = cudaFuncSetAttribute(k_nlist, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     // the row builder is latency-bound: launch as many CTAs as fit
     *nl_blocks_per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(nl_blocks_per_sm, k_nlist, 128, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(nl_blocks_per_sm, k_nlist, NL_THREADS, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_persist<HD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
     if (e != cudaSuccess) return e;
@@ -1950,7 +1952,9 @@ void launch_rebuild_prep(const Dev &D, cudaStream_t s) {
     k_bin<<<D.nl_grid, 256, 0, s>>>(D);
     k_cellsort<<<D.nl_grid, 128, 4 * D.cell_cap * sizeof(int), s>>>(D);
 }
-void launch_nlist(const Dev &D, cudaStream_t s) { k_nlist<<<D.nl_grid, 128, nl_smem_bytes(D), s>>>(D); }
+void launch_nlist(const Dev &D, cudaStream_t s) {
+    k_nlist<<<D.nl_grid, NL_THREADS, nl_smem_bytes(D, NL_THREADS / 32), s>>>(D);
+}
 void launch_rebuild(const Dev &D, cudaStream_t s) {
     launch_rebuild_prep(D, s);
     launch_nlist(D, s);

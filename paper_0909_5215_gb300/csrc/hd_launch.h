@@ -22,7 +22,7 @@ void launch_qinit(const Dev &Q, const Dev &M, cudaStream_t s);
 void launch_qiter(const Dev &Q, int max_iter, cudaStream_t s);  // 8 kernels
 void launch_qdisp(const Dev &Q, cudaStream_t s);
 void launch_adopt(const Dev &Q, const Dev &M, const int *adopt, cudaStream_t s);
-size_t nl_smem_bytes(const Dev &D);                               // dynamic shared memory of the list build
+size_t nl_smem_bytes(const Dev &D, int nwarps);                  // dynamic shared memory of the list build
 // allow that much on the kernels that build lists; *nl_blocks_per_sm: resident row-build CTAs per SM
 cudaError_t nl_configure(const Dev &D, int *nl_blocks_per_sm);
 int persist_blocks_per_sm(const Dev &D);                          // resident CTAs of the persistent kernel
