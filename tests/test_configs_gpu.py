@@ -7,7 +7,7 @@
   positions, about 5.36M atoms, stepped by the per-phase kernels.
 
 For sampled replicas the lists must equal the oracle's bit for bit, the
-split-form forces must be within 1e-5 RMS relative (spec bound for the
+split-form forces must be within 1e-5 RMS relative (the stated bound for the
 FP32 path), and the Maxwell-Boltzmann draws within 1e-6.  Then 100 steps run
 with the slope bias (Eq. 14) inside its band: each sampled replica's band is
 the 10%-90% range of sigma over an unbiased oracle pre-run of the same 100
