@@ -419,6 +419,35 @@ def test_gated_quench_gives_the_full_quench_answer(oracle_mod):
     assert o2.transition(xg2, theta)[0] == 1 and _maxdisp(sl, xg2) > 0.9
 
 
+def test_gated_quench_on_a_3d_model(oracle_mod):
+    """3-D: from a thermal state around the minimum the in-basin stop comes
+    sooner, within theta - keep of the full quench's minimum and unflagged;
+    against an r_O moved by 0.6 sigma it never applies (the quench equals the
+    full one, flagged)."""
+    base = small3d()
+    o = oracle_mod.OracleReplica(base, _params())
+    xstar, _, _ = o.quench(method=1, ftol=1e-8, max_iter=40000)
+    ref = base.copy()
+    ref.pos, ref.pos_ref = xstar.copy(), xstar.copy()
+    theta, keep = 0.5, 0.25
+    st = ref.copy()
+    st.pos = thermalise(ref, amp=0.02, seed=5).pos
+    o1 = oracle_mod.OracleReplica(st, _params())
+    xf, itf, ff = o1.quench(method=1, ftol=1e-4, max_iter=40000, step_size=0.005)
+    xg, itg, fg = o1.quench(method=1, ftol=1e-4, max_iter=40000, step_size=0.005, ftol_stay=1e-1, keep=keep)
+    assert ff < 1e-4 and fg < 1e-1 and itg < itf
+    assert _maxdisp(st, xg) < keep and np.abs(xg - xf).max() < theta - keep
+    assert o1.transition(xg, theta)[0] == o1.transition(xf, theta)[0] == 0
+    far = st.copy()
+    far.pos_ref = st.pos_ref.copy()
+    far.pos_ref[:, 0] += 0.6
+    o2 = oracle_mod.OracleReplica(far, _params())
+    xf2, itf2, _ = o2.quench(method=1, ftol=1e-4, max_iter=40000, step_size=0.005)
+    xg2, itg2, _ = o2.quench(method=1, ftol=1e-4, max_iter=40000, step_size=0.005, ftol_stay=1e-1, keep=keep)
+    assert itg2 == itf2 and np.array_equal(xg2, xf2)
+    assert o2.transition(xg2, theta)[0] == 1
+
+
 def test_diverging_quench_stops_cleanly(oracle_mod):
     """Steepest descent with a step beyond 2 / (largest curvature) runs away
     from a thermal configuration of the paper's 2-D model: the quench must
