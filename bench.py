@@ -174,7 +174,7 @@ def prepare_batch(reps, params, driver, block, split, setup_md=1000, pair_kernel
     b.quench(method=1, ftol=seed_ftol or (1e-3 if split else 1e-6), max_iter=20000, step_size=QSTEP, theta=1e30,
              adopt=2)
     ob = b.obs()
-    b.seed_quench = {"converged": int(ob[:, 27].sum()), "of": len(reps), "iters_max": int(ob[:, 14].max()),
+    b.seed_quench = {"converged": int((ob[:, 27] == 1).sum()), "of": len(reps), "iters_max": int(ob[:, 14].max()),
                      "fmax_max": float(ob[:, 15].max())}
     if setup_md > 0:
         b.step(setup_md)
