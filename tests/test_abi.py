@@ -216,3 +216,26 @@ def test_nose_hoover_chain_reaches_the_descriptor(hdlib):
     descs, _keep = hdlib.make_descs([r])
     from paper_0909_5215_gb300 import model as M
     assert hdlib.hd_workspace_bytes(descs, 1, hdlib.make_params(M.Params())) == 0
+
+
+def test_quench_statistics_split_the_three_outcomes():
+    """Batch.qstats reads HD_OBS_QCONV's three codes (1 reached ftol, 2
+    stopped inside the basin, 0 stopped at max_iter) into separate fractions
+    and largest forces; no GPU is needed for this host logic."""
+    from paper_0909_5215_gb300 import hd
+
+    class Fake:
+        pass
+
+    f = Fake()
+    ob = np.zeros((5, hd.OBS_LEN))
+    ob[:, 14] = [100, 40, 40, 300, 120]        # q_iter
+    ob[:, 15] = [0.009, 0.08, 0.05, 2.5, 0.004]  # q_fmax
+    ob[:, 27] = [1, 2, 2, 0, 1]                # q_conv
+    f.obs = lambda: ob
+    f.last_flags = np.array([1, 0, 0, 0, 0], np.int32)
+    q = hd.Batch.qstats(f)
+    assert q["iters"] == pytest.approx(120.0) and q["iters_max"] == 300
+    assert q["converged"] == pytest.approx(0.4) and q["stayed"] == pytest.approx(0.4)
+    assert q["fmax"] == 0.009 and q["fmax_stay"] == 0.08 and q["fmax_unconverged"] == 2.5
+    assert q["flagged"] == 1
