@@ -204,7 +204,9 @@ enum {
     HD_FIELD_ENERGY = 10       /* double [n] per-atom LJ energy (half of each pair)   */
 };
 
-/* OBS record, doubles */
+/* OBS record, doubles.  K is the kinetic energy at the end of the last step
+ * of the last hd_step call (between the steps of one call the library does
+ * not form it). */
 enum {
     HD_OBS_STEP = 0, HD_OBS_TMD = 1, HD_OBS_TH = 2, HD_OBS_V = 3, HD_OBS_K = 4,
     HD_OBS_DV = 5, HD_OBS_SIGMA = 6, HD_OBS_D = 7, HD_OBS_FR = 8, HD_OBS_XT = 9,
