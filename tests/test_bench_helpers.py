@@ -62,3 +62,18 @@ def test_committed_traffic_is_tied_to_the_sources(monkeypatch):
         assert t is None
     monkeypatch.setattr(bench, "kernel_code_hash", lambda: "0" * 16)
     assert bench.committed_traffic(True) is None
+
+
+def test_quench_summary_reports_the_three_outcomes():
+    import argparse
+    args = argparse.Namespace(quench_ftol=1e-2, quench_stay=1e-1, quench_iters=3000)
+    qs = [{"iters": 400.0, "iters_max": 1200, "converged": 0.1, "stayed": 0.9, "fmax": 0.009, "fmax_stay": 0.09,
+           "fmax_unconverged": 0.0, "flagged": 1},
+          {"iters": 500.0, "iters_max": 3000, "converged": 0.0, "stayed": 0.8, "fmax": 0.0, "fmax_stay": 0.095,
+           "fmax_unconverged": 0.5, "flagged": 0}]
+    s = bench.quench_summary(qs, args, ms=100.0, md_ms=60.0, seed={"converged": 2, "of": 2})
+    assert s["iters_mean"] == pytest.approx(450.0) and s["iters_max"] == 3000
+    assert s["converged_fraction"] == pytest.approx(0.05) and s["stayed_fraction"] == pytest.approx(0.85)
+    assert s["unconverged_fraction"] == pytest.approx(0.10)
+    assert s["fmax_max_converged"] == 0.009 and s["fmax_max_stayed"] == 0.095 and s["fmax_max_unconverged"] == 0.5
+    assert s["flagged"] == 1 and s["time_share"] == pytest.approx(0.4) and s["ftol_stay"] == 1e-1
